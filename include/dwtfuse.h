@@ -1,0 +1,152 @@
+/*
+ * libdwtfuse -- one-level 2D DWT pansharpening on one GPU (sm_103a).
+ *
+ * The method is that of Al-Oraiqat, Bashkov, Babkov, Titarenko, "Fusion of
+ * multispectral satellite imagery using a cluster of graphics processing unit"
+ * (arXiv:1803.00737), Sec. 2: forward 2D DWT of the panchromatic image (PAN),
+ * replacement of the approximation (LL) subband by a multispectral (MS) band,
+ * inverse 2D DWT, once per MS band.  Wavelets: Haar (Eq. 1-2, 11-12) and
+ * Daubechies-4 with periodic wrap (Eq. 3-10, 13-16).
+ *
+ * Conventions shared by every entry point:
+ *  - All image pointers are DEVICE pointers owned by the caller; the library
+ *    never frees or keeps them.  Arrays of per-band pointers (ms, grad_ms) are
+ *    HOST arrays of `bands` device pointers.
+ *  - Images are dense row-major.  PAN and fused bands are H x W; MS bands are
+ *    (H/2) x (W/2).  Fused outputs and output gradients are planar
+ *    [bands][H][W] in one allocation.
+ *  - H and W are even; Haar needs H, W >= 2, D4 needs H, W >= 4.  1 <= bands
+ *    <= DWTFUSE_MAX_BANDS.  Otherwise DWTFUSE_ESHAPE.
+ *  - MS pointers must be aligned to their element size; PAN, output and
+ *    gradient-image pointers to twice their element size (they are accessed
+ *    as pixel pairs); otherwise DWTFUSE_EALIGN.  W a multiple of 4 with
+ *    16-byte-aligned float / 4-byte-aligned uint8 images enables the
+ *    4-pixel vector path.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously; the call returns once it is enqueued.
+ *  - The arithmetic is FP32.  Inputs are uint8 (DWTFUSE_U8) or float
+ *    (DWTFUSE_F32).  uint8 outputs are clamp(round-half-even(v), 0, 255).
+ *  - The LL replacement is LL <- gain * MS with gain 1 for Haar (the 2 x 2 mean
+ *    is the Haar approximation) and 2 for D4 (its 2D low-pass has DC gain 2).
+ *  - Errors are returned as dwtfuse_status codes; nothing aborts the process.
+ *    A CUDA failure is DWTFUSE_ECUDA (see dwtfuse_last_cuda_error).  No entry
+ *    point allocates device memory.
+ */
+#ifndef DWTFUSE_H
+#define DWTFUSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DWTFUSE_OK = 0,
+    DWTFUSE_EINVAL = 1,   /* NULL pointer, bad enum, bad count                */
+    DWTFUSE_ESHAPE = 2,   /* odd or too small H/W, too many bands             */
+    DWTFUSE_EALIGN = 3,   /* pointer not aligned to its element size          */
+    DWTFUSE_ENOMEM = 4,   /* caller workspace too small                       */
+    DWTFUSE_ECUDA = 5,    /* a CUDA runtime call or launch failed             */
+    DWTFUSE_ETIMEOUT = 6, /* a bounded device-side wait gave up               */
+    DWTFUSE_EDEVICE = 7   /* a device-side check failed (see device status)   */
+} dwtfuse_status;
+
+typedef enum { DWTFUSE_HAAR = 0, DWTFUSE_D4 = 1 } dwtfuse_wavelet;
+typedef enum { DWTFUSE_U8 = 0, DWTFUSE_F32 = 1 } dwtfuse_dtype;
+
+#define DWTFUSE_MAX_BANDS 16
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *dwtfuse_status_string(int status);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int dwtfuse_version(void);
+
+/* cudaError_t value behind the last DWTFUSE_ECUDA returned on this thread
+ * (0 if none).  The library clears the CUDA error it reports. */
+int dwtfuse_last_cuda_error(void);
+
+/*
+ * Fused forward (Sec. 2 step list; Eq. 1-16): for each band b,
+ *   F_b = IDWT2( DWT2(PAN) with LL <- gain * MS_b ).
+ * One pass over HBM: the PAN low-pass is computed once per tile and shared by
+ * all bands, and the detail subbands are never materialised (by linearity,
+ * F_b = PAN + U(gain * MS_b - LL(PAN)), U = synthesis of an LL-only image).
+ *   pan      H x W, in_dtype
+ *   ms       host array of `bands` device pointers, each (H/2) x (W/2), in_dtype
+ *   out_f32  [bands][H][W] float, or NULL
+ *   out_u8   [bands][H][W] uint8 (clamped, rounded half to even), or NULL
+ * At least one of out_f32 / out_u8 must be non-NULL; both are written in the
+ * same pass when both are given.  Outputs must not overlap inputs.
+ */
+int dwtfuse_fuse(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                 int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *stream);
+
+/*
+ * Adjoint (vector-Jacobian product) of dwtfuse_fuse with respect to PAN and
+ * every MS band, for float images.  With U and LL as above and S the
+ * synthesis matrix (S = A^T for D4, S = 2 A^T for the /2 Haar of Eq. 1-2, so
+ * the transpose is not the inverse):
+ *   grad_ms_b = gain * sigma^2 * LL(grad_out_b)
+ *   grad_pan  = G - U(LL(G)),  G = sum_b grad_out_b
+ * (sigma = 2 for Haar, 1 for D4).
+ *   grad_out  [bands][H][W] float
+ *   grad_pan  H x W float (overwritten)
+ *   grad_ms   host array of `bands` device pointers, each (H/2) x (W/2) float
+ *             (overwritten)
+ */
+int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W, int wavelet,
+                          float *grad_pan, float *const *grad_ms, void *stream);
+
+/* One scene of a batched call (all pointers on the device, as above). */
+typedef struct {
+    const void *pan;
+    const void *ms[DWTFUSE_MAX_BANDS];
+    float *out_f32;   /* [bands][H][W] or NULL */
+    uint8_t *out_u8;  /* [bands][H][W] or NULL */
+    int64_t H, W;
+    int32_t bands;
+    int32_t wavelet;  /* dwtfuse_wavelet */
+    int32_t in_dtype; /* dwtfuse_dtype   */
+    int32_t reserved; /* must be 0       */
+} dwtfuse_scene;
+
+#define DWTFUSE_MAX_SCENES 128
+
+/* Bytes of device workspace dwtfuse_fuse_batched needs (queue counter and
+ * device status word). */
+size_t dwtfuse_batched_workspace_size(void);
+
+/*
+ * Batched fused forward: up to DWTFUSE_MAX_SCENES scenes of any legal sizes,
+ * band counts (<= 8 per scene), wavelets and input types in ONE persistent
+ * launch.  Warps pull (scene, tile) work items from a device-side queue whose
+ * counter lives in `workspace`; the scene table travels in the kernel's
+ * parameter block, so the call is capturable in a CUDA graph (the capture
+ * records a memset of the counter and the kernel; the host array `scenes`
+ * may be freed after the call).  Results equal dwtfuse_fuse per scene.
+ *   rows_per_item  MS rows per work item (0 = library default)
+ *   blocks_per_sm  resident CTAs per SM for the persistent grid (0 = max)
+ */
+int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, size_t ws_bytes,
+                         int rows_per_item, int blocks_per_sm, void *stream);
+
+/*
+ * Reads (synchronously, on `stream`) the device status word of a batched
+ * workspace: DWTFUSE_OK, or the first device-side error recorded.
+ */
+int dwtfuse_get_last_device_status(const void *workspace, void *stream);
+
+/*
+ * Launch-shape knob of dwtfuse_fuse for the autotuner: MS rows per warp work
+ * item (0 restores the default).  Process-wide; not thread-safe.
+ */
+int dwtfuse_set_rows_per_item(int rows);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DWTFUSE_H */

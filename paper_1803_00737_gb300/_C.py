@@ -1,0 +1,199 @@
+"""ctypes binding of libdwtfuse (include/dwtfuse.h): argument marshalling only.
+
+Every function here checks that tensors live on a CUDA device and are dense,
+turns them into pointers, sizes and the current torch stream, and calls the C
+entry point of the same name.  There is no CPU path: if the library is not
+built, or a tensor is not on the GPU, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from .build import LIB
+
+OK, EINVAL, ESHAPE, EALIGN, ENOMEM, ECUDA, ETIMEOUT, EDEVICE = range(8)
+HAAR, D4 = 0, 1
+U8, F32 = 0, 1
+MAX_BANDS = 16
+MAX_SCENES = 128
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+
+
+class DwtfuseError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = lib().dwtfuse_status_string(status).decode()
+        if status == ECUDA:
+            msg += f" (cudaError {lib().dwtfuse_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [status {status}]")
+
+
+class Scene(ctypes.Structure):
+    """dwtfuse_scene of include/dwtfuse.h."""
+    _fields_ = [
+        ("pan", _vp),
+        ("ms", _vp * MAX_BANDS),
+        ("out_f32", _vp),
+        ("out_u8", _vp),
+        ("H", _i64),
+        ("W", _i64),
+        ("bands", ctypes.c_int32),
+        ("wavelet", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+_SIGS = {
+    "dwtfuse_status_string": (ctypes.c_char_p, [_i]),
+    "dwtfuse_version": (_i, []),
+    "dwtfuse_last_cuda_error": (_i, []),
+    "dwtfuse_fuse": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp]),
+    "dwtfuse_fuse_backward": (_i, [_vp, _i, _i64, _i64, _i, _vp, ctypes.POINTER(_vp), _vp]),
+    "dwtfuse_batched_workspace_size": (_sz, []),
+    "dwtfuse_fuse_batched": (_i, [ctypes.POINTER(Scene), _i, _vp, _sz, _i, _i, _vp]),
+    "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
+    "dwtfuse_set_rows_per_item": (_i, [_i]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libdwtfuse.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(
+                    f"{LIB} is missing: build it with paper_1803_00737_gb300.build.build() "
+                    "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue  # reported by the symbol test, raised on use
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str) -> None:
+    if status != OK:
+        raise DwtfuseError(status, what)
+
+
+def _dev(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (libdwtfuse has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _dtype_code(t: torch.Tensor, name: str) -> int:
+    if t.dtype == torch.uint8:
+        return U8
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"{name} must be uint8 or float32, got {t.dtype}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _bands(ms) -> list[torch.Tensor]:
+    if isinstance(ms, torch.Tensor):
+        return [ms[b] for b in range(ms.shape[0])] if ms.dim() == 3 else [ms]
+    return list(ms)
+
+
+def dwtfuse_fuse(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None = None,
+                 out_u8: torch.Tensor | None = None, stream=None) -> None:
+    """Fused forward into caller-provided outputs (see dwtfuse_fuse in dwtfuse.h)."""
+    bands = _bands(ms)
+    H, W = pan.shape
+    code = _dtype_code(pan, "pan")
+    ptrs = (_vp * len(bands))(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
+    for b, m in enumerate(bands):
+        if m.dtype != pan.dtype or tuple(m.shape) != (H // 2, W // 2):
+            raise ValueError(f"ms[{b}] must be {pan.dtype} of shape ({H // 2}, {W // 2})")
+    for name, o, dt in (("out_f32", out_f32, torch.float32), ("out_u8", out_u8, torch.uint8)):
+        if o is not None and (o.dtype != dt or tuple(o.shape) != (len(bands), H, W)):
+            raise ValueError(f"{name} must be {dt} of shape ({len(bands)}, {H}, {W})")
+    st = lib().dwtfuse_fuse(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet), code,
+                            _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                            _dev(out_u8, "out_u8") if out_u8 is not None else None,
+                            _stream(stream))
+    _check(st, "dwtfuse_fuse")
+
+
+def dwtfuse_fuse_backward(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.Tensor,
+                          grad_ms, stream=None) -> None:
+    """Adjoint of the fusion into caller-provided gradient buffers."""
+    B, H, W = grad_out.shape
+    if grad_out.dtype != torch.float32 or grad_pan.dtype != torch.float32:
+        raise TypeError("gradients must be float32")
+    gms = _bands(grad_ms)
+    if len(gms) != B:
+        raise ValueError("one grad_ms buffer per band")
+    ptrs = (_vp * B)(*[_dev(g, f"grad_ms[{b}]") for b, g in enumerate(gms)])
+    st = lib().dwtfuse_fuse_backward(_dev(grad_out, "grad_out"), B, H, W, int(wavelet),
+                                     _dev(grad_pan, "grad_pan"), ptrs, _stream(stream))
+    _check(st, "dwtfuse_fuse_backward")
+
+
+def dwtfuse_batched_workspace_size() -> int:
+    return int(lib().dwtfuse_batched_workspace_size())
+
+
+def make_scene(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
+               out_u8: torch.Tensor | None = None) -> Scene:
+    bands = _bands(ms)
+    s = Scene()
+    s.pan = _dev(pan, "pan")
+    for b, m in enumerate(bands):
+        s.ms[b] = _dev(m, f"ms[{b}]")
+    s.out_f32 = _dev(out_f32, "out_f32") if out_f32 is not None else None
+    s.out_u8 = _dev(out_u8, "out_u8") if out_u8 is not None else None
+    s.H, s.W = pan.shape
+    s.bands = len(bands)
+    s.wavelet = int(wavelet)
+    s.in_dtype = _dtype_code(pan, "pan")
+    s.reserved = 0
+    return s
+
+
+def dwtfuse_fuse_batched(scenes: list[Scene], workspace: torch.Tensor, rows_per_item: int = 0,
+                         blocks_per_sm: int = 0, stream=None) -> None:
+    """One persistent launch over all scenes (capturable in a CUDA graph)."""
+    arr = (Scene * len(scenes))(*scenes)
+    st = lib().dwtfuse_fuse_batched(arr, len(scenes), _dev(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(),
+                                    int(rows_per_item), int(blocks_per_sm), _stream(stream))
+    _check(st, "dwtfuse_fuse_batched")
+
+
+def dwtfuse_get_last_device_status(workspace: torch.Tensor, stream=None) -> int:
+    return int(lib().dwtfuse_get_last_device_status(_dev(workspace, "workspace"), _stream(stream)))
+
+
+def dwtfuse_set_rows_per_item(rows: int) -> None:
+    _check(lib().dwtfuse_set_rows_per_item(int(rows)), "dwtfuse_set_rows_per_item")

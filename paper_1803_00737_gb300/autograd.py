@@ -1,0 +1,55 @@
+"""Differentiable fusion: torch.autograd.Function over the forward and adjoint
+kernels of libdwtfuse.
+
+The fusion is linear in (PAN, MS), so the backward needs no saved
+activations: it applies the transpose of the fused map (dwtfuse_fuse_backward)
+to the incoming gradient.  Only shapes and the wavelet are kept in ctx.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _C
+
+
+class DWTFuseFn(torch.autograd.Function):
+    """fused = DWTFuseFn.apply(pan, ms, wavelet)
+
+    pan: (N, H, W) or (H, W) float32 CUDA; ms: (N, B, H/2, W/2) or (B, H/2, W/2)
+    float32 CUDA.  Returns (N, B, H, W) or (B, H, W) float32.
+    """
+
+    @staticmethod
+    def forward(ctx, pan: torch.Tensor, ms: torch.Tensor, wavelet: int):
+        batched = pan.dim() == 3
+        P = pan if batched else pan.unsqueeze(0)
+        M = ms if batched else ms.unsqueeze(0)
+        P = P.contiguous()
+        M = M.contiguous()
+        N, H, W = P.shape
+        B = M.shape[1]
+        if M.shape != (N, B, H // 2, W // 2):
+            raise ValueError("ms must be (N, B, H/2, W/2) matching pan (N, H, W)")
+        out = torch.empty((N, B, H, W), dtype=torch.float32, device=P.device)
+        for i in range(N):
+            _C.dwtfuse_fuse(P[i], M[i], wavelet, out[i], None)
+        ctx.wavelet = int(wavelet)
+        ctx.batched = batched
+        ctx.shape = (N, B, H, W)
+        return out if batched else out[0]
+
+    @staticmethod
+    def backward(ctx, grad: torch.Tensor):
+        N, B, H, W = ctx.shape
+        g = (grad if ctx.batched else grad.unsqueeze(0)).contiguous().float()
+        gp = torch.empty((N, H, W), dtype=torch.float32, device=g.device)
+        gm = torch.empty((N, B, H // 2, W // 2), dtype=torch.float32, device=g.device)
+        for i in range(N):
+            _C.dwtfuse_fuse_backward(g[i], ctx.wavelet, gp[i], gm[i])
+        if not ctx.batched:
+            gp, gm = gp[0], gm[0]
+        return gp, gm, None
+
+
+def dwt_fuse(pan: torch.Tensor, ms: torch.Tensor, wavelet: int) -> torch.Tensor:
+    return DWTFuseFn.apply(pan, ms, wavelet)

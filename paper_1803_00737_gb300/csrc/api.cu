@@ -1,0 +1,211 @@
+// C ABI of libdwtfuse: argument validation, launch-shape selection and
+// dispatch to the kernels.  Declarations and the contract are in dwtfuse.h.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "dwtfuse.h"
+#include "launch.h"
+
+namespace dwtfuse {
+
+namespace {
+std::mutex g_mu;
+std::unordered_map<const void *, int> g_occ;
+std::unordered_map<int, int> g_sms;
+std::atomic<int> g_rows{kDefaultRows};
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+}  // namespace
+
+cudaError_t resident_blocks(const void *fn, int threads, int *out) {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_occ.find(fn);
+        if (it != g_occ.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_occ[fn] = occ;
+    *out = occ;
+    return cudaSuccess;
+}
+
+cudaError_t sm_count(int *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_sms.find(dev);
+        if (it != g_sms.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+    }
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_sms[dev] = n;
+    *out = n;
+    return cudaSuccess;
+}
+
+int rows_per_item() { return g_rows.load(std::memory_order_relaxed); }
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DWTFUSE_OK;
+    g_last_cuda = e;
+    return DWTFUSE_ECUDA;
+}
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+constexpr int64_t kMaxSide = int64_t(1) << 20;  // 1 Mi px per side
+
+int check_shape(int64_t H, int64_t W, int wavelet) {
+    if (wavelet != DWTFUSE_HAAR && wavelet != DWTFUSE_D4) return DWTFUSE_EINVAL;
+    const int64_t lo = wavelet == DWTFUSE_D4 ? 4 : 2;
+    if (H < lo || W < lo || (H & 1) || (W & 1) || H > kMaxSide || W > kMaxSide)
+        return DWTFUSE_ESHAPE;
+    return DWTFUSE_OK;
+}
+
+// Validates one scene and fills its kernel arguments.
+int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+               int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, int max_bands,
+               SceneArgs *s) {
+    if (!pan || !ms || (!out_f32 && !out_u8)) return DWTFUSE_EINVAL;
+    if (in_dtype != DWTFUSE_U8 && in_dtype != DWTFUSE_F32) return DWTFUSE_EINVAL;
+    const int st = check_shape(H, W, wavelet);
+    if (st != DWTFUSE_OK) return st;
+    if (bands < 1) return DWTFUSE_EINVAL;
+    if (bands > max_bands) return DWTFUSE_ESHAPE;
+    const uintptr_t es = in_dtype == DWTFUSE_F32 ? 4 : 1;
+    // PAN is read as pixel pairs and outputs are written as pixel pairs.
+    if (!aligned(pan, 2 * es) || (out_f32 && !aligned(out_f32, 8)) || (out_u8 && !aligned(out_u8, 2)))
+        return DWTFUSE_EALIGN;
+    std::memset(s, 0, sizeof *s);
+    for (int b = 0; b < bands; ++b) {
+        if (!ms[b]) return DWTFUSE_EINVAL;
+        if (!aligned(ms[b], es)) return DWTFUSE_EALIGN;
+        s->ms[b] = ms[b];
+    }
+    s->pan = pan;
+    s->out_f32 = out_f32;
+    s->out_u8 = out_u8;
+    s->H = H;
+    s->W = W;
+    s->bands = bands;
+    s->wavelet = wavelet;
+    s->in_f32 = in_dtype == DWTFUSE_F32;
+    s->gain = wavelet == DWTFUSE_D4 ? 2.0f : 1.0f;
+    s->a4 = (W % 4 == 0) && aligned(pan, 4 * es) && (!out_f32 || aligned(out_f32, 16)) &&
+            (!out_u8 || aligned(out_u8, 4));
+    return DWTFUSE_OK;
+}
+
+}  // namespace dwtfuse
+
+using namespace dwtfuse;
+
+extern "C" {
+
+const char *dwtfuse_status_string(int status) {
+    switch (status) {
+        case DWTFUSE_OK: return "ok";
+        case DWTFUSE_EINVAL: return "invalid argument (NULL pointer, bad enum or count)";
+        case DWTFUSE_ESHAPE: return "unsupported shape (H, W must be even, >= 2 Haar / >= 4 D4; band count)";
+        case DWTFUSE_EALIGN: return "misaligned pointer";
+        case DWTFUSE_ENOMEM: return "workspace too small";
+        case DWTFUSE_ECUDA: return "CUDA runtime error";
+        case DWTFUSE_ETIMEOUT: return "bounded device wait timed out";
+        case DWTFUSE_EDEVICE: return "device-side check failed";
+        default: return "unknown status";
+    }
+}
+
+int dwtfuse_version(void) { return 100; }
+
+int dwtfuse_last_cuda_error(void) { return (int)g_last_cuda; }
+
+int dwtfuse_set_rows_per_item(int rows) {
+    if (rows < 0 || rows > 4096) return DWTFUSE_EINVAL;
+    g_rows.store(rows == 0 ? kDefaultRows : rows, std::memory_order_relaxed);
+    return DWTFUSE_OK;
+}
+
+int dwtfuse_fuse(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                 int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *stream) {
+    SceneArgs s;
+    const int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
+    if (st != DWTFUSE_OK) return st;
+    return cuda_status(launch_fuse(s, rows_per_item(), 0, static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W, int wavelet,
+                          float *grad_pan, float *const *grad_ms, void *stream) {
+    if (!grad_out || !grad_pan || !grad_ms) return DWTFUSE_EINVAL;
+    const int st = check_shape(H, W, wavelet);
+    if (st != DWTFUSE_OK) return st;
+    if (bands < 1) return DWTFUSE_EINVAL;
+    if (bands > kMaxBands) return DWTFUSE_ESHAPE;
+    if (!aligned(grad_out, 8) || !aligned(grad_pan, 8)) return DWTFUSE_EALIGN;
+    for (int b = 0; b < bands; ++b) {
+        if (!grad_ms[b]) return DWTFUSE_EINVAL;
+        if (!aligned(grad_ms[b], 4)) return DWTFUSE_EALIGN;
+    }
+    return cuda_status(launch_fuse_backward(grad_out, bands, H, W, wavelet, grad_pan, grad_ms,
+                                            rows_per_item(), static_cast<cudaStream_t>(stream)));
+}
+
+size_t dwtfuse_batched_workspace_size(void) { return 256; }
+
+int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, size_t ws_bytes,
+                         int rows_per_item_, int blocks_per_sm, void *stream) {
+    if (!scenes || n < 1 || !workspace || rows_per_item_ < 0 || blocks_per_sm < 0)
+        return DWTFUSE_EINVAL;
+    if (n > kMaxScenes) return DWTFUSE_ESHAPE;
+    if (ws_bytes < dwtfuse_batched_workspace_size()) return DWTFUSE_ENOMEM;
+    if (!aligned(workspace, 16)) return DWTFUSE_EALIGN;
+    static thread_local BatchTable t;  // ~27 KB: kept off the stack
+    std::memset(&t, 0, sizeof t);
+    t.n = n;
+    t.R = rows_per_item_ > 0 ? rows_per_item_ : kDefaultRows;
+    int64_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+        const dwtfuse_scene &d = scenes[i];
+        if (d.reserved != 0) return DWTFUSE_EINVAL;
+        const int st = make_scene(d.pan, d.ms, d.bands, d.H, d.W, d.wavelet, d.in_dtype, d.out_f32,
+                                  d.out_u8, kBatchMaxBands, &t.scenes[i]);
+        if (st != DWTFUSE_OK) return st;
+        const ItemGrid g = item_grid(d.H, d.W, t.R);
+        t.item_start[i] = acc;
+        t.strips_x[i] = g.strips_x;
+        acc += g.items;
+    }
+    t.item_start[n] = acc;
+    auto *queue = static_cast<unsigned long long *>(workspace);
+    int *status = reinterpret_cast<int *>(static_cast<char *>(workspace) + 8);
+    return cuda_status(launch_fuse_batched(t, queue, status, blocks_per_sm, static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_get_last_device_status(const void *workspace, void *stream) {
+    if (!workspace) return DWTFUSE_EINVAL;
+    int v = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(workspace) + 8, sizeof v,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return v;
+}
+
+}  // extern "C"

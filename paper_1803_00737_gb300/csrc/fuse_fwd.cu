@@ -1,0 +1,132 @@
+// Fused forward kernels: the single-scene grid-stride kernel and the batched
+// persistent kernel fed by a device-side work queue.
+#include "fuse_tile.cuh"
+#include "launch.h"
+
+namespace dwtfuse {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// Single scene, bands [b0, b0 + NB).  Each warp takes work items
+// warp, warp + total_warps, ... (grid sized to the resident capacity).
+template <typename T, int WAV, int NB>
+__global__ void __launch_bounds__(kThreads, 2)
+fuse_fwd_kernel(const __grid_constant__ SceneArgs s, int b0, int64_t strips_x, int64_t items, int R) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); it < items; it += nwarps)
+        run_item<T, WAV, NB>(s, it, strips_x, R, b0, NB, lane);
+}
+
+// Batched: every warp pulls the next item index from `queue[0]`; item ranges
+// of the scenes are given by the prefix sums item_start[].  A warp whose
+// scene table entry fails its checks records DWTFUSE_EDEVICE in status[0].
+__global__ void __launch_bounds__(kThreads, 2)
+fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *queue, int *status) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)t.item_start[t.n];
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        int lo = 0, hi = t.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)t.item_start[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const SceneArgs &s = t.scenes[lo];
+        if (s.bands < 1 || s.bands > kBatchMaxBands) {
+            if (lane == 0) atomicCAS(status, 0, 7);
+            continue;
+        }
+        const int64_t local = (int64_t)(it - (unsigned long long)t.item_start[lo]);
+        const int64_t sx = t.strips_x[lo];
+        // Bands in chunks of kBatchChunk: the PAN low-pass of a chunk's rows is
+        // recomputed (from L1/L2) instead of holding state for 8 bands.
+        for (int b0 = 0; b0 < s.bands; b0 += kBatchChunk) {
+            const int nb = min(kBatchChunk, s.bands - b0);
+            if (s.in_f32)
+                run_item<float, -1, kBatchChunk>(s, local, sx, t.R, b0, nb, lane);
+            else
+                run_item<uint8_t, -1, kBatchChunk>(s, local, sx, t.R, b0, nb, lane);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+template <typename T, int WAV, int NB>
+void *fwd_fn() { return reinterpret_cast<void *>(&fuse_fwd_kernel<T, WAV, NB>); }
+
+template <typename T, int WAV>
+void *fwd_fn_nb(int nb) {
+    switch (nb) {
+        case 1: return fwd_fn<T, WAV, 1>();
+        case 2: return fwd_fn<T, WAV, 2>();
+        case 3: return fwd_fn<T, WAV, 3>();
+        case 4: return fwd_fn<T, WAV, 4>();
+        case 5: return fwd_fn<T, WAV, 5>();
+        case 6: return fwd_fn<T, WAV, 6>();
+        case 7: return fwd_fn<T, WAV, 7>();
+        default: return fwd_fn<T, WAV, 8>();
+    }
+}
+
+void *fwd_kernel_ptr(bool f32, int wav, int nb) {
+    if (f32) return wav ? fwd_fn_nb<float, 1>(nb) : fwd_fn_nb<float, 0>(nb);
+    return wav ? fwd_fn_nb<uint8_t, 1>(nb) : fwd_fn_nb<uint8_t, 0>(nb);
+}
+
+}  // namespace
+
+cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream) {
+    const ItemGrid g = item_grid(s.H, s.W, R);
+    for (int b0 = 0; b0 < s.bands; b0 += kChunkBands) {
+        const int nb = s.bands - b0 < kChunkBands ? s.bands - b0 : kChunkBands;
+        void *fn = fwd_kernel_ptr(s.in_f32 != 0, s.wavelet, nb);
+        int occ = 0;
+        cudaError_t e = resident_blocks(fn, kThreads, &occ);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+        int sms = 0;
+        e = sm_count(&sms);
+        if (e != cudaSuccess) return e;
+        const int64_t need = (g.items + kWarps - 1) / kWarps;
+        const int64_t cap = (int64_t)sms * occ;
+        const unsigned grid = (unsigned)(need < cap ? need : cap);
+        if (grid == 0) continue;
+        SceneArgs sa = s;
+        int64_t strips_x = g.strips_x, items = g.items;
+        void *args[] = {&sa, (void *)&b0, &strips_x, &items, &R};
+        e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
+                                int blocks_per_sm, cudaStream_t stream) {
+    void *fn = reinterpret_cast<void *>(&fuse_batched_kernel);
+    int occ = 0;
+    cudaError_t e = resident_blocks(fn, kThreads, &occ);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+    int sms = 0;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(queue, 0, kQueueBytes, stream);
+    if (e != cudaSuccess) return e;
+    const int64_t total = t.item_start[t.n];
+    const int64_t need = (total + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)sms * occ;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    if (grid == 0) return cudaSuccess;
+    fuse_batched_kernel<<<grid, kThreads, 0, stream>>>(t, queue, status);
+    return cudaGetLastError();
+}
+
+}  // namespace dwtfuse

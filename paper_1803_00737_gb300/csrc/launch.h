@@ -1,0 +1,40 @@
+// Internal launch interface between the C ABI (api.cu) and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fuse_tile.cuh"
+
+namespace dwtfuse {
+
+constexpr int kChunkBands = 8;     // bands per single-scene launch (more = several launches)
+constexpr int kBatchMaxBands = 8;  // bands per scene in the batched kernel
+constexpr int kBatchChunk = 4;     // bands processed together by one batched work item pass
+constexpr int kMaxScenes = 128;    // scenes per batched launch
+constexpr int kDefaultRows = 32;   // MS rows per warp work item
+constexpr size_t kQueueBytes = 16; // queue counter (8) + status word (4) + pad
+
+// Scene table of a batched launch.  It travels by value in the kernel
+// parameter block (< 32 KB), so a captured graph owns its own copy.
+struct BatchTable {
+    int32_t n;
+    int32_t R;
+    int64_t item_start[kMaxScenes + 1];
+    int64_t strips_x[kMaxScenes];
+    SceneArgs scenes[kMaxScenes];
+};
+static_assert(sizeof(BatchTable) + 16 <= 32764, "batched scene table exceeds the parameter limit");
+
+// Resident CTAs per SM for a kernel at a block size (cached per kernel).
+cudaError_t resident_blocks(const void *fn, int threads, int *out);
+// SM count of the current device (cached per device).
+cudaError_t sm_count(int *out);
+
+cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream);
+cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
+                                 float *gpan, float *const *gms, int R, cudaStream_t stream);
+cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
+                                int blocks_per_sm, cudaStream_t stream);
+
+}  // namespace dwtfuse

@@ -1,0 +1,128 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and its argument validation answers before any GPU work.
+No GPU needed (every call here returns from validation)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1803_00737_gb300 import _C
+from paper_1803_00737_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return _C.lib()
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(dwtfuse_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("dwtfuse_fuse", "dwtfuse_fuse_batched", "dwtfuse_fuse_backward",
+                 "dwtfuse_status_string", "dwtfuse_get_last_device_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert not [n for n in declared_symbols() if n not in _C._SIGS]
+
+
+def test_status_strings(L):
+    for code in range(8):
+        assert L.dwtfuse_status_string(code)
+    assert L.dwtfuse_status_string(99) == b"unknown status"
+
+
+FAKE = 0x10000  # never dereferenced: every call below fails validation first
+
+
+def _ms(n, addr=FAKE):
+    return (ctypes.c_void_p * n)(*([addr] * n))
+
+
+@pytest.mark.parametrize("H,W,wav,code", [
+    (5, 4, 0, _C.ESHAPE), (4, 6, 1, _C.OK), (2, 2, 1, _C.ESHAPE), (0, 4, 0, _C.ESHAPE),
+    (4, 3, 0, _C.ESHAPE), (4, 4, 2, _C.EINVAL), (1 << 21, 4, 0, _C.ESHAPE)])
+def test_shape_validation(L, H, W, wav, code):
+    if code == _C.OK:
+        pytest.skip("valid shapes would launch")
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 1, H, W, wav, _C.U8, FAKE, None, None) == code
+
+
+def test_null_and_count_validation(L):
+    assert L.dwtfuse_fuse(None, _ms(1), 1, 4, 4, 0, _C.U8, FAKE, None, None) == _C.EINVAL
+    assert L.dwtfuse_fuse(FAKE, None, 1, 4, 4, 0, _C.U8, FAKE, None, None) == _C.EINVAL
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 1, 4, 4, 0, _C.U8, None, None, None) == _C.EINVAL
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 0, 4, 4, 0, _C.U8, FAKE, None, None) == _C.EINVAL
+    assert L.dwtfuse_fuse(FAKE, _ms(17), 17, 4, 4, 0, _C.U8, FAKE, None, None) == _C.ESHAPE
+    assert L.dwtfuse_fuse(FAKE, _ms(2, 0), 2, 4, 4, 0, _C.U8, FAKE, None, None) == _C.EINVAL
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 1, 4, 4, 0, 7, FAKE, None, None) == _C.EINVAL
+
+
+def test_alignment_validation(L):
+    # float PAN must be 8-byte aligned (pixel pairs), float out 8-byte, uint8 out 2-byte
+    assert L.dwtfuse_fuse(FAKE + 4, _ms(1), 1, 4, 4, 0, _C.F32, FAKE, None, None) == _C.EALIGN
+    assert L.dwtfuse_fuse(FAKE + 1, _ms(1), 1, 4, 4, 0, _C.U8, FAKE, None, None) == _C.EALIGN
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 1, 4, 4, 0, _C.U8, FAKE + 4, None, None) == _C.EALIGN
+    assert L.dwtfuse_fuse(FAKE, _ms(1), 1, 4, 4, 0, _C.U8, None, FAKE + 1, None) == _C.EALIGN
+    assert L.dwtfuse_fuse(FAKE, _ms(1, FAKE + 2), 1, 4, 4, 0, _C.F32, FAKE, None, None) == _C.EALIGN
+
+
+def test_backward_validation(L):
+    gms = _ms(2)
+    assert L.dwtfuse_fuse_backward(None, 2, 4, 4, 0, FAKE, gms, None) == _C.EINVAL
+    assert L.dwtfuse_fuse_backward(FAKE, 2, 4, 5, 0, FAKE, gms, None) == _C.ESHAPE
+    assert L.dwtfuse_fuse_backward(FAKE + 4, 2, 4, 4, 0, FAKE, gms, None) == _C.EALIGN
+    assert L.dwtfuse_fuse_backward(FAKE, 0, 4, 4, 0, FAKE, gms, None) == _C.EINVAL
+
+
+def test_batched_validation(L):
+    s = _C.Scene()
+    s.pan = FAKE
+    s.ms[0] = FAKE
+    s.out_f32 = FAKE
+    s.H, s.W, s.bands, s.wavelet, s.in_dtype = 4, 4, 9, 0, 0
+    arr = (_C.Scene * 1)(s)
+    ws = _C.lib().dwtfuse_batched_workspace_size()
+    assert ws >= 16
+    assert L.dwtfuse_fuse_batched(arr, 1, FAKE, ws, 0, 0, None) == _C.ESHAPE  # 9 bands > 8
+    s.bands = 1
+    arr = (_C.Scene * 1)(s)
+    assert L.dwtfuse_fuse_batched(arr, 1, FAKE, ws - 1, 0, 0, None) == _C.ENOMEM
+    assert L.dwtfuse_fuse_batched(arr, 0, FAKE, ws, 0, 0, None) == _C.EINVAL
+    assert L.dwtfuse_fuse_batched(arr, 129, FAKE, ws, 0, 0, None) == _C.ESHAPE
+    s.reserved = 1
+    arr = (_C.Scene * 1)(s)
+    assert L.dwtfuse_fuse_batched(arr, 1, FAKE, ws, 0, 0, None) == _C.EINVAL
+
+
+def test_rows_knob(L):
+    assert L.dwtfuse_set_rows_per_item(-1) == _C.EINVAL
+    assert L.dwtfuse_set_rows_per_item(16) == _C.OK
+    assert L.dwtfuse_set_rows_per_item(0) == _C.OK
+
+
+def test_cpu_tensors_are_rejected():
+    torch = pytest.importorskip("torch")
+    pan = torch.zeros((4, 4), dtype=torch.uint8)
+    ms = torch.zeros((1, 2, 2), dtype=torch.uint8)
+    with pytest.raises(ValueError, match="CUDA"):
+        _C.dwtfuse_fuse(pan, ms, 0, torch.zeros((1, 4, 4)), None)
