@@ -140,6 +140,35 @@ int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, si
 int dwtfuse_get_last_device_status(const void *workspace, void *stream);
 
 /*
+ * Batched fused forward that needs no device memory from the caller and
+ * allocates none itself.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * It serves callers that cannot allocate device memory when they call:
+ * applications that reserve all of the GPU's memory up front in their own
+ * pool (a new allocation would fail or fragment it), plug-in hosts that hand
+ * the library only image pointers, and real-time processing chains whose
+ * memory footprint must be fixed at start-up.  dwtfuse_fuse_batched needs a
+ * caller workspace for its work-queue counter; this variant keeps that counter
+ * and the device status word in a DWTFUSE_STATIC_SCRATCH_BYTES-byte array in
+ * the library's device code, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ * Arguments and results are those of dwtfuse_fuse_batched without the
+ * workspace.  More than DWTFUSE_MAX_SCENES scenes is DWTFUSE_ESHAPE; a launch
+ * whose queue needs more scratch than the array holds is DWTFUSE_ENOMEM.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents; each
+ * call clears the counter and status word on its stream before its kernel.
+ * Calls that overlap on the GPU (unordered streams) race on the counter, so
+ * order them.  The device status word is not reported by this entry point.
+ */
+#define DWTFUSE_STATIC_SCRATCH_BYTES 256
+int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, int rows_per_item,
+                                 int blocks_per_sm, void *stream);
+
+/*
  * Launch-shape knob of dwtfuse_fuse for the autotuner: MS rows per warp work
  * item (0 restores the default).  Process-wide; not thread-safe.
  */

@@ -62,6 +62,7 @@ _SIGS = {
     "dwtfuse_fuse_batched": (_i, [ctypes.POINTER(Scene), _i, _vp, _sz, _i, _i, _vp]),
     "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
     "dwtfuse_set_rows_per_item": (_i, [_i]),
+    "dwtfuse_fuse_batched_noalloc": (_i, [ctypes.POINTER(Scene), _i, _i, _i, _vp]),
 }
 
 _lock = threading.Lock()
@@ -189,6 +190,16 @@ def dwtfuse_fuse_batched(scenes: list[Scene], workspace: torch.Tensor, rows_per_
                                     workspace.numel() * workspace.element_size(),
                                     int(rows_per_item), int(blocks_per_sm), _stream(stream))
     _check(st, "dwtfuse_fuse_batched")
+
+
+def dwtfuse_fuse_batched_noalloc(scenes: list[Scene], rows_per_item: int = 0,
+                                 blocks_per_sm: int = 0, stream=None) -> None:
+    """Batched launch for callers that cannot allocate device memory: the queue
+    counter lives in the library's own static device array (see dwtfuse.h)."""
+    arr = (Scene * len(scenes))(*scenes)
+    st = lib().dwtfuse_fuse_batched_noalloc(arr, len(scenes), int(rows_per_item),
+                                            int(blocks_per_sm), _stream(stream))
+    _check(st, "dwtfuse_fuse_batched_noalloc")
 
 
 def dwtfuse_get_last_device_status(workspace: torch.Tensor, stream=None) -> int:
