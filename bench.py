@@ -4,7 +4,8 @@
 Workload (one step): Daubechies-4 fusion of a Landsat-7-shaped synthetic scene,
 PAN 16384 x 16384 uint8 with 6 MS bands 8192 x 8192 uint8 (periodic wrap, LL
 gain 2), writing every fused band both as float32 and as rounded uint8 in one
-pass.  Inputs are generated on the device from a seed (scenegen).
+pass, then ERGAS and QNR of the uint8 product on the GPU.  Inputs are
+generated on the device from a seed (scenegen).
 
   value     fused Gpx/s = PAN pixels x bands per second, inputs resident in HBM
   e2e       the same metric with the inputs copied host -> device from pinned
@@ -12,6 +13,10 @@ pass.  Inputs are generated on the device from a seed (scenegen).
   roofline  fused-forward kernel: algorithmic bytes per launch / mean launch
             time (CUDA events on the launch stream) against the measured HBM
             copy bandwidth
+  forms     the other forms of the path, timed after the main region on their
+            own workloads: 96 uneven scenes through one captured batched launch,
+            and forward + backward of a batch of 8 float32 4096^2 scenes (4 bands)
+            next to the plain forward of the same batch
 
 Multi-GPU: the path does not shard here (replicas only): each rank fuses its
 own scene, timing is the max over ranks, value sums every rank's pixels.
@@ -36,7 +41,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fused Gpx/s (PAN px × bands) and % HBM roofline; fwd+bwd Gpx/s vs plain fwd"
 UNIT = "Gpx/s"
-H = W = 16384
+H = W = 16384  # overridden by --side (profiling cases only)
 BANDS = 6
 WAVELET = 1  # Daubechies-4
 BLOB_SCALE = 16.0
@@ -58,11 +63,13 @@ def kernel_hash() -> str:
 def workload_config() -> dict:
     return {
         "workload": f"D4 DWT fusion, PAN {H}x{W} uint8, {BANDS} MS bands {H // 2}x{W // 2} uint8, "
-                    "float32 + uint8 fused output in one pass",
+                    "float32 + uint8 fused output in one pass, then ERGAS + QNR (32x32 windows) "
+                    "of the uint8 product",
         "wavelet": "daubechies4_periodic",
         "pan": [H, W],
         "bands": BANDS,
         "outputs": ["float32", "uint8"],
+        "metrics": ["ERGAS", "QNR", "D_lambda", "D_s"],
         "l2": "inputs and outputs (8.7 GB per step) exceed L2; no flush needed",
         "parallelism": "replicas",
     }
@@ -178,8 +185,19 @@ def barrier(world: int) -> None:
 
 # ------------------------------------------------------------------ CPU oracle (baseline only)
 
+def oracle_step(pan, ms, pan_u8, ms_u8) -> None:
+    """One step of the path in the oracle: FP64 fusion, the uint8 product, and
+    ERGAS + QNR of that product."""
+    import oracle as O
+    fused = O.fuse(pan, ms, WAVELET)
+    u8 = O.to_u8(fused)
+    del fused
+    O.ergas(u8, list(ms_u8))
+    O.qnr(u8, list(ms_u8), pan_u8)
+
+
 def oracle_rate(pan_u8, ms_u8, min_seconds: float, max_reps: int) -> tuple[float, int, float, int]:
-    """Oracle FP64 fusion rate on a host sample: (Gpx/s, threads, seconds, reps)."""
+    """Oracle rate of the whole step on a host sample: (Gpx/s, threads, seconds, reps)."""
     import numpy as np
 
     import oracle as O
@@ -188,7 +206,7 @@ def oracle_rate(pan_u8, ms_u8, min_seconds: float, max_reps: int) -> tuple[float
     units = pan.size * ms.shape[0]
     reps, t0 = 0, time.perf_counter()
     while True:
-        O.fuse(pan, ms, WAVELET)
+        oracle_step(pan, ms, pan_u8, ms_u8)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds or reps >= max_reps:
@@ -209,14 +227,14 @@ def run_reference(args) -> None:
     import oracle as O
     pf, mf = pan.astype(np.float64), ms.astype(np.float64)
     for _ in range(args.warmup):
-        O.fuse(pf, mf, WAVELET)
+        oracle_step(pf, mf, pan, ms)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.fuse(pf, mf, WAVELET)
+        oracle_step(pf, mf, pan, ms)
     el = time.perf_counter() - t0
     value = side * side * BANDS * args.steps / el / 1e9
-    sample = (f"FP64 oracle, D4 fusion of a {side}x{side} PAN crop-size scene with {BANDS} "
-              f"bands (same generator), per step")
+    sample = (f"FP64 oracle, D4 fusion of a {side}x{side} PAN scene with {BANDS} bands (same "
+              f"generator) + ERGAS/QNR of the uint8 product, per step")
     cpu = {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -229,8 +247,149 @@ def run_reference(args) -> None:
 
 # ------------------------------------------------------------------ GPU arm
 
+def measure_e2e(args, pan, ms, out_u, res, step, stream, world, dev) -> dict:
+    """Same step with pinned host inputs copied in and the uint8 fused bands and
+    the four quality figures copied out inside the timed region."""
+    import torch
+    pan_h = pan.cpu().pin_memory()
+    ms_h = ms.cpu().pin_memory()
+    out_h = torch.empty((BANDS, H, W), dtype=torch.uint8).pin_memory()
+    res_h = torch.empty(4, dtype=torch.float64).pin_memory()
+    Ke = max(1, min(args.steps, args.e2e_steps))
+    for _ in range(2):
+        pan.copy_(pan_h, non_blocking=True)
+        ms.copy_(ms_h, non_blocking=True)
+        step()
+        out_h.copy_(out_u, non_blocking=True)
+        res_h.copy_(res, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        pan.copy_(pan_h, non_blocking=True)
+        ms.copy_(ms_h, non_blocking=True)
+        step()
+        out_h.copy_(out_u, non_blocking=True)
+        res_h.copy_(res, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e_el, e_units = aggregate(e0.elapsed_time(e1) / 1e3, float(H * W * BANDS * Ke), world, dev)
+    return {"value": e_units / e_el / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": pan.numel() + ms.numel(),
+           "d2h_bytes_per_step": out_u.numel() + res.numel() * 8,
+           "steps": Ke}
+
+
+def _time_ms(fn, reps: int, stream) -> float:
+    """Mean milliseconds of fn() over reps runs (CUDA events on `stream`)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_forms(args, dev, peak: float, world: int) -> dict:
+    """Batched (96 uneven scenes, one captured persistent launch) and autograd
+    (batch 8 x 4096^2 float32, 4 bands: forward + backward vs plain forward)."""
+    import torch
+
+    import scenegen
+    from paper_1803_00737_gb300 import _C
+    out = {}
+    stream = torch.cuda.current_stream()
+    reps = max(1, args.form_reps)
+
+    # -- batched: 96 scenes, sides U[256, 8192], 3-8 bands, Haar/D4, float32 out
+    specs = scenegen.batch_specs(n=96, seed=0)
+    keep, scenes = [], []
+    px_bands = 0.0
+    nbytes = 0.0
+    for sp in specs:
+        p, m = scenegen.make_scene(sp.H, sp.W, sp.bands, seed=sp.seed, device=dev)
+        o = torch.empty((sp.bands, sp.H, sp.W), dtype=torch.float32, device=dev)
+        keep.append((p, m, o))
+        scenes.append(_C.make_scene(p, m, sp.wavelet, o, None))
+        px_bands += sp.H * sp.W * sp.bands
+        nbytes += sp.H * sp.W * (1.0 + sp.bands * (0.25 + 4.0))
+    ws = torch.zeros(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=dev)
+    _C.dwtfuse_fuse_batched(scenes, ws)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        _C.dwtfuse_fuse_batched(scenes, ws)
+    g.replay()
+    ms_b = _time_ms(g.replay, reps, stream)
+    out["batched"] = {
+        "workload": "96 scenes, PAN sides even U[256, 8192] (independent H, W), 3-8 bands, "
+                    "Haar/D4 mixed, uint8 in, float32 out, one persistent launch in a CUDA graph",
+        "value": px_bands / (ms_b / 1e3) / 1e9, "unit": UNIT, "ms": ms_b,
+        "roofline": {"achieved": nbytes / (ms_b / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": nbytes / (ms_b / 1e3) / 1e9 / peak},
+        "gpu_launches_per_replay": 1,
+    }
+    del keep, scenes, g
+    torch.cuda.empty_cache()
+
+    # -- autograd: batch 8 of PAN 4096^2 float32 with 4 MS bands
+    N, B, S = 8, 4, 4096
+    pans, mss = [], []
+    for i in range(N):
+        p, m = scenegen.make_scene(S, S, B, seed=i, device=dev)
+        pans.append(p.float())
+        mss.append(m.float())
+    P = torch.stack(pans)
+    M = torch.stack(mss)
+    del pans, mss
+    F = torch.empty((N, B, S, S), dtype=torch.float32, device=dev)
+    G = scenegen.target_like((N, B, S, S), seed=1000, device=dev)
+    gp = torch.empty((N, S, S), dtype=torch.float32, device=dev)
+    gm = torch.empty((N, B, S // 2, S // 2), dtype=torch.float32, device=dev)
+
+    def fwd_all():
+        for i in range(N):
+            _C.dwtfuse_fuse(P[i], M[i], WAVELET, F[i], None)
+
+    def bwd_all():
+        for i in range(N):
+            _C.dwtfuse_fuse_backward(G[i], WAVELET, gp[i], gm[i])
+
+    def fwd_bwd():
+        fwd_all()
+        bwd_all()
+
+    for f in (fwd_all, bwd_all):
+        f()
+    ms_f = _time_ms(fwd_all, reps, stream)
+    ms_bw = _time_ms(bwd_all, reps, stream)
+    ms_fb = _time_ms(fwd_bwd, reps, stream)
+    units = N * B * S * S
+    fbytes = N * S * S * (4.0 + B * (1.0 + 4.0))
+    bbytes = N * S * S * (4.0 * B + 4.0 + B)
+    out["autograd"] = {
+        "workload": "D4, batch 8 x PAN 4096^2 float32, 4 MS bands 2048^2 float32; forward "
+                    "(float32 out) + adjoint backward (grad PAN, grad MS)",
+        "fwd_bwd": units / (ms_fb / 1e3) / 1e9, "plain_fwd": units / (ms_f / 1e3) / 1e9,
+        "unit": UNIT, "ratio_fwd_bwd_to_fwd": ms_f / ms_fb,
+        "fwd_ms": ms_f, "bwd_ms": ms_bw, "fwd_bwd_ms": ms_fb,
+        "roofline_fwd": {"achieved": fbytes / (ms_f / 1e3) / 1e9, "frac": fbytes / (ms_f / 1e3) / 1e9 / peak},
+        "roofline_bwd": {"achieved": bbytes / (ms_bw / 1e3) / 1e9, "frac": bbytes / (ms_bw / 1e3) / 1e9 / peak},
+        "gpu_launches_per_pass": 2 * N,
+    }
+    return out
+
+
 def run_ours(args) -> None:
     import torch
+
+    global H, W
+    H = W = args.side
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -247,12 +406,22 @@ def run_ours(args) -> None:
     pan, ms = scenegen.make_scene(H, W, BANDS, seed=rank, blob_scale=BLOB_SCALE, device=dev)
     out_f = torch.empty((BANDS, H, W), dtype=torch.float32, device=dev)
     out_u = torch.empty((BANDS, H, W), dtype=torch.uint8, device=dev)
+    mws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
+    res = torch.zeros(4, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def fwd():
         _C.dwtfuse_fuse(pan, ms, WAVELET, out_f, out_u)
 
-    launches_per_step = (BANDS + 7) // 8
+    def metrics():
+        _C.dwtfuse_metrics(out_u, ms, pan, mws, res)
+
+    def step():
+        fwd()
+        metrics()
+
+    fwd_launches = (BANDS + 7) // 8
+    launches_per_step = fwd_launches + 3  # + metric passes at PAN and MS size, finalize
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -261,57 +430,38 @@ def run_ours(args) -> None:
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else None)
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(K)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     sampler.start()
+    torch.cuda.nvtx.range_push("timed")
     t_start.record(stream)
     for k in range(K):
         ev[k][0].record(stream)
-        step()
+        fwd()
         ev[k][1].record(stream)
+        metrics()
+        ev[k][2].record(stream)
     t_end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier(world)
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    fwd_ms = [a.elapsed_time(b) for a, b in ev]
+    fwd_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    met_ms = [b.elapsed_time(c) for _, b, c in ev]
+    quality = res.cpu().tolist()
     units = float(H * W * BANDS * K)
     max_el, total_units = aggregate(elapsed, units, world, dev)
     value = total_units / max_el / 1e9
 
-    # end to end: pinned host inputs in, uint8 fused bands out, every step
-    pan_h = pan.cpu().pin_memory()
-    ms_h = ms.cpu().pin_memory()
-    out_h = torch.empty((BANDS, H, W), dtype=torch.uint8).pin_memory()
-    Ke = max(1, min(K, args.e2e_steps))
-    for _ in range(2):
-        pan.copy_(pan_h, non_blocking=True)
-        ms.copy_(ms_h, non_blocking=True)
-        step()
-        out_h.copy_(out_u, non_blocking=True)
-    torch.cuda.synchronize()
-    barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(Ke):
-        pan.copy_(pan_h, non_blocking=True)
-        ms.copy_(ms_h, non_blocking=True)
-        step()
-        out_h.copy_(out_u, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    e_el, e_units = aggregate(e0.elapsed_time(e1) / 1e3, float(H * W * BANDS * Ke), world, dev)
-    e2e = {"value": e_units / e_el / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": pan.numel() + ms.numel(),
-           "d2h_bytes_per_step": out_u.numel(),
-           "steps": Ke}
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, pan, ms, out_u, res, step, stream, world, dev)
 
     peak, peak_kind = measured_hbm()
-    mean_fwd_s = statistics.mean(fwd_ms) / 1e3 / launches_per_step
+    mean_fwd_s = statistics.mean(fwd_ms) / 1e3 / fwd_launches
     achieved = fwd_bytes_per_launch() / mean_fwd_s / 1e9
     kh = kernel_hash()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -323,14 +473,20 @@ def run_ours(args) -> None:
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        side = args.cpu_side
+        side = min(args.cpu_side, H)
         pan_c = pan[:side, :side].cpu().numpy()
         ms_c = ms[:, :side // 2, :side // 2].cpu().numpy()
-        rate, cores, secs, reps = oracle_rate(pan_c, ms_c, args.cpu_seconds, 5)
+        rate, cores, secs, reps = oracle_rate(pan_c, ms_c, args.cpu_seconds, 20)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle D4 fusion of the top-left {side}x{side} PAN crop with its "
-                         f"{BANDS} MS crops (periodic wrap at the crop), {reps} rep(s), "
-                         f"{secs:.1f} s"}
+               "sample": f"FP64 oracle step (D4 fusion + ERGAS/QNR of the uint8 product) on the "
+                         f"top-left {side}x{side} PAN crop with its {BANDS} MS crops (periodic "
+                         f"wrap at the crop), {reps} rep(s), {secs:.1f} s"}
+
+    forms = None
+    if not args.no_forms:
+        del out_f
+        torch.cuda.empty_cache()
+        forms = measure_forms(args, dev, peak, world)
 
     if rank == 0:
         print(json.dumps({
@@ -340,6 +496,10 @@ def run_ours(args) -> None:
             "config": workload_config(), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches_per_step * K, "clocks": clocks,
             "fwd_ms": {"mean": statistics.mean(fwd_ms), "min": min(fwd_ms), "max": max(fwd_ms)},
+            "metrics_ms": {"mean": statistics.mean(met_ms), "min": min(met_ms), "max": max(met_ms)},
+            "fwd_only_gpxs": H * W * BANDS / (statistics.mean(fwd_ms) / 1e3) / 1e9,
+            "quality": dict(zip(["ERGAS", "QNR", "D_lambda", "D_s"], quality)),
+            "forms": forms,
         }))
     if world > 1:
         import torch.distributed as dist
@@ -357,6 +517,11 @@ def main() -> None:
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-side", type=int, default=4096, help="PAN side of a reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--form-reps", type=int, default=10)
+    ap.add_argument("--side", type=int, default=16384,
+                    help="PAN side (default: the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -100,6 +100,48 @@ int dwtfuse_fuse(const void *pan, const void *const *ms, int bands, int64_t H, i
 int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W, int wavelet,
                           float *grad_pan, float *const *grad_ms, void *stream);
 
+/*
+ * Quality metrics of a fused product.  The paper reports ERGAS and QNR
+ * (Sec. 4, Table 3) without defining them; the definitions used are:
+ *   ERGAS    = 100 * (1/2) * sqrt( (1/B) sum_b RMSE_b^2 / mu_b^2 ), RMSE_b over
+ *              all H x W pixels against MS_b repeated 2 x 2, mu_b = mean of MS_b;
+ *   Q        = Wang-Bovik index on non-overlapping 32 x 32 windows at each
+ *              image's own resolution, averaged (ragged edge dropped; a zero
+ *              denominator gives 1 for identical windows, else 0);
+ *   D_lambda = mean over ordered band pairs |Q(F_l, F_r) - Q(MS_l, MS_r)|;
+ *   D_s      = mean over bands |Q(F_l, PAN) - Q(MS_l, PAN~)|, PAN~ = 2 x 2 block
+ *              mean of PAN;  QNR = (1 - D_lambda)(1 - D_s).
+ *   fused     [bands][H][W], fused_dtype (uint8 or float)
+ *   ms        host array of `bands` device pointers, (H/2) x (W/2), in_dtype
+ *   pan       H x W, in_dtype
+ *   window    must be DWTFUSE_QNR_WINDOW (32)
+ *   workspace dwtfuse_metrics_workspace_size() bytes of device memory, 8-byte
+ *             aligned; its contents are scratch between calls
+ * bands <= DWTFUSE_METRIC_MAX_BANDS (8).  QNR needs H/2, W/2 >= window.
+ * Results are deterministic (fixed reduction order).
+ */
+#define DWTFUSE_QNR_WINDOW 32
+#define DWTFUSE_METRIC_MAX_BANDS 8
+
+size_t dwtfuse_metrics_workspace_size(void);
+
+/* Asynchronous on `stream`: writes four doubles to DEVICE memory out_device:
+ * ERGAS, QNR, D_lambda, D_s.  Capturable in a CUDA graph. */
+int dwtfuse_metrics(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
+                    int in_dtype, int bands, int64_t H, int64_t W, int window, void *workspace,
+                    size_t ws_bytes, double *out_device, void *stream);
+
+/* ERGAS only (pan not needed); waits for the stream and writes the HOST double. */
+int dwtfuse_ergas(const void *fused, int fused_dtype, const void *const *ms, int in_dtype,
+                  int bands, int64_t H, int64_t W, void *workspace, size_t ws_bytes,
+                  double *out_ergas, void *stream);
+
+/* QNR, D_lambda and D_s; waits for the stream and writes HOST doubles. */
+int dwtfuse_qnr(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
+                int in_dtype, int bands, int64_t H, int64_t W, int window, void *workspace,
+                size_t ws_bytes, double *out_qnr, double *out_dlambda, double *out_ds,
+                void *stream);
+
 /* One scene of a batched call (all pointers on the device, as above). */
 typedef struct {
     const void *pan;

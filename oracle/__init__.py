@@ -31,6 +31,7 @@ _lib = None
 _D = ctypes.POINTER(ctypes.c_double)
 _U8 = ctypes.POINTER(ctypes.c_uint8)
 _L = ctypes.POINTER(ctypes.c_long)
+_V = ctypes.c_void_p
 
 
 def build(force: bool = False) -> str:
@@ -67,10 +68,10 @@ def _load():
                 "oracle_fuse_adjoint": (i, [i, l, l, i, d, _D, _D, ctypes.POINTER(_D)]),
                 "oracle_fuse_points": (i, [i, l, l, d, _D, _U8, _D, _U8, l, _L, _L, _D]),
                 "oracle_to_u8": (None, [l, _D, _U8]),
-                "oracle_ergas": (d, [l, l, i, _D, ctypes.POINTER(_D)]),
-                "oracle_q_index": (d, [l, l, _D, _D, l]),
-                "oracle_qnr": (i, [l, l, i, _D, ctypes.POINTER(_D), _D, l,
-                                   ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
+                "oracle_ergas_t": (d, [l, l, i, _V, i, ctypes.POINTER(_V), i]),
+                "oracle_q_index_t": (d, [l, l, _V, i, _V, i, l]),
+                "oracle_qnr_t": (i, [l, l, i, _V, i, ctypes.POINTER(_V), i, _V, i, l,
+                                     ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]),
                 "oracle_num_threads": (i, []),
                 "oracle_set_threads": (None, [i]),
             }
@@ -242,35 +243,55 @@ def to_u8(x) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- metrics
+# Metric inputs may be uint8 (the 8-bit product) or float; uint8 arrays are
+# read as such, anything else is converted to float64.
+
+def _img(a):
+    a = np.asarray(a)
+    if a.dtype == np.uint8:
+        a = np.ascontiguousarray(a)
+        return a, 1
+    return _f64(a), 0
+
+
+def _imgs(arrs):
+    conv = [_img(a) for a in arrs]
+    types = {t for _, t in conv}
+    if len(types) != 1:
+        raise ValueError("all MS bands must share one dtype")
+    ptrs = (_V * len(conv))(*[a.ctypes.data for a, _ in conv])
+    return conv, ptrs, types.pop()
+
 
 def ergas(fused, ms) -> float:
     """ERGAS of fused (B, H, W) against MS (B, H/2, W/2); definition in dwt_oracle.c."""
-    fused = _f64(fused)
-    ms = [_f64(m) for m in ms]
-    B, H, W = fused.shape
-    return float(_load().oracle_ergas(H, W, B, _p(fused), _ptr_array(ms)))
+    f, ft = _img(fused)
+    B, H, W = f.shape
+    keep, ptrs, mt = _imgs(list(ms))
+    return float(_load().oracle_ergas_t(H, W, B, f.ctypes.data, ft, ptrs, mt))
 
 
 def q_index(x, y, win: int = 32) -> float:
     """Wang-Bovik Q averaged over non-overlapping win x win windows."""
-    x = _f64(x)
-    y = _f64(y)
+    x, xt = _img(x)
+    y, yt = _img(y)
     if x.shape != y.shape:
         raise ValueError("shape mismatch")
-    return float(_load().oracle_q_index(x.shape[0], x.shape[1], _p(x), _p(y), int(win)))
+    return float(_load().oracle_q_index_t(x.shape[0], x.shape[1], x.ctypes.data, xt, y.ctypes.data,
+                                          yt, int(win)))
 
 
 def qnr(fused, ms, pan, win: int = 32):
     """(QNR, D_lambda, D_s); definition in dwt_oracle.c."""
-    fused = _f64(fused)
-    ms = [_f64(m) for m in ms]
-    pan = _f64(pan)
-    B, H, W = fused.shape
+    f, ft = _img(fused)
+    B, H, W = f.shape
+    keep, ptrs, mt = _imgs(list(ms))
+    p, pt = _img(pan)
     q = ctypes.c_double()
     dl = ctypes.c_double()
     ds = ctypes.c_double()
-    _check(_load().oracle_qnr(H, W, B, _p(fused), _ptr_array(ms), _p(pan), int(win),
-                              ctypes.byref(q), ctypes.byref(dl), ctypes.byref(ds)), "qnr")
+    _check(_load().oracle_qnr_t(H, W, B, f.ctypes.data, ft, ptrs, mt, p.ctypes.data, pt, int(win),
+                                ctypes.byref(q), ctypes.byref(dl), ctypes.byref(ds)), "qnr")
     return q.value, dl.value, ds.value
 
 

@@ -449,21 +449,36 @@ void oracle_to_u8(long n, const double *x, uint8_t *y) {
 
 /* ------------------------------------------------------------ metrics */
 
+/* Images given to the metrics are either FP64 or uint8 (the 8-bit product);
+ * every value is read as a double. */
+#define ORACLE_F64 0
+#define ORACLE_U8 1
+
+static double img_at(const void *base, int type, long idx) {
+    return type == ORACLE_U8 ? (double)((const uint8_t *)base)[idx] : ((const double *)base)[idx];
+}
+
+static const void *img_plane(const void *base, int type, long offset) {
+    return type == ORACLE_U8 ? (const void *)((const uint8_t *)base + offset)
+                             : (const void *)((const double *)base + offset);
+}
+
 /* ERGAS (Sec. 4, Table 3; the paper gives no formula).  Definition used:
  *   ERGAS = 100 * (d_h / d_l) * sqrt( (1/B) sum_b RMSE_b^2 / mu_b^2 ),
  * d_h / d_l = 1/2 (PAN is twice the MS resolution per side, Sec. 2), the
  * reference for band b is MS_b repeated 2 x 2 to PAN size, RMSE_b is taken
  * over all H x W pixels and mu_b is the mean of that reference.
  * fused: B x H x W; ms: B arrays of H/2 x W/2. */
-double oracle_ergas(long H, long W, int B, const double *fused, const double *const *ms) {
+double oracle_ergas_t(long H, long W, int B, const void *fused, int ftype, const void *const *ms,
+                      int mtype) {
     const long W2 = W / 2, n = H * W;
     double acc = 0.0;
     for (int b = 0; b < B; ++b) {
         double se = 0.0, sum = 0.0;
         for (long y = 0; y < H; ++y)
             for (long x = 0; x < W; ++x) {
-                const double ref = ms[b][(y / 2) * W2 + x / 2];
-                const double d = fused[(long)b * n + y * W + x] - ref;
+                const double ref = img_at(ms[b], mtype, (y / 2) * W2 + x / 2);
+                const double d = img_at(fused, ftype, (long)b * n + y * W + x) - ref;
                 se += d * d;
                 sum += ref;
             }
@@ -473,17 +488,22 @@ double oracle_ergas(long H, long W, int B, const double *fused, const double *co
     return 100.0 * 0.5 * sqrt(acc / (double)B);
 }
 
+double oracle_ergas(long H, long W, int B, const double *fused, const double *const *ms) {
+    return oracle_ergas_t(H, W, B, fused, ORACLE_F64, (const void *const *)ms, ORACLE_F64);
+}
+
 /* Universal image quality index of Wang and Bovik on one window:
  *   Q = 4 s_xy mu_x mu_y / ((s_x^2 + s_y^2) (mu_x^2 + mu_y^2)),
  * population (co)variances.  A zero denominator gives 1 if the two windows are
- * identical and 0 otherwise. */
-static double q_window(const double *x, const double *y, long stride, long win) {
+ * identical and 0 otherwise.  (x0, y0 index the window's top-left pixel.) */
+static double q_window(const void *x, int xt, const void *y, int yt, long stride, long off,
+                       long win) {
     const double n = (double)(win * win);
     double mx = 0.0, my = 0.0;
     for (long r = 0; r < win; ++r)
         for (long s = 0; s < win; ++s) {
-            mx += x[r * stride + s];
-            my += y[r * stride + s];
+            mx += img_at(x, xt, off + r * stride + s);
+            my += img_at(y, yt, off + r * stride + s);
         }
     mx /= n;
     my /= n;
@@ -491,7 +511,8 @@ static double q_window(const double *x, const double *y, long stride, long win) 
     int same = 1;
     for (long r = 0; r < win; ++r)
         for (long s = 0; s < win; ++s) {
-            const double a = x[r * stride + s], b = y[r * stride + s];
+            const double a = img_at(x, xt, off + r * stride + s);
+            const double b = img_at(y, yt, off + r * stride + s);
             vx += (a - mx) * (a - mx);
             vy += (b - my) * (b - my);
             cxy += (a - mx) * (b - my);
@@ -507,17 +528,26 @@ static double q_window(const double *x, const double *y, long stride, long win) 
 
 /* Q averaged over the non-overlapping win x win windows of two h x w images
  * (windows at multiples of win; a ragged right/bottom edge is dropped).
- * Returns NAN if no full window fits. */
-double oracle_q_index(long h, long w, const double *x, const double *y, long win) {
+ * Windows are evaluated in parallel into a per-window array and summed in
+ * window order.  Returns NAN if no full window fits. */
+double oracle_q_index_t(long h, long w, const void *x, int xt, const void *y, int yt, long win) {
     const long ny = h / win, nx = w / win;
     if (ny < 1 || nx < 1) return NAN;
+    double *q = (double *)malloc(sizeof(double) * ny * nx);
+    if (!q) return NAN;
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < ny * nx; ++k) {
+        const long wy = k / nx, wx = k % nx;
+        q[k] = q_window(x, xt, y, yt, w, wy * win * w + wx * win, win);
+    }
     double acc = 0.0;
-    for (long wy = 0; wy < ny; ++wy)
-        for (long wx = 0; wx < nx; ++wx) {
-            const long off = wy * win * w + wx * win;
-            acc += q_window(x + off, y + off, w, win);
-        }
+    for (long k = 0; k < ny * nx; ++k) acc += q[k];
+    free(q);
     return acc / (double)(ny * nx);
+}
+
+double oracle_q_index(long h, long w, const double *x, const double *y, long win) {
+    return oracle_q_index_t(h, w, x, ORACLE_F64, y, ORACLE_F64, win);
 }
 
 /* QNR (Sec. 4, Table 3; the paper gives no formula).  Definition used, with
@@ -528,33 +558,38 @@ double oracle_q_index(long h, long w, const double *x, const double *y, long win
  *   QNR      = (1 - D_lambda) (1 - D_s)
  * Q is oracle_q_index with win x win windows, at PAN size for F and PAN and at
  * MS size for MS and PAN~.  B = 1 gives D_lambda = 0.
- * fused: B x H x W; ms: B arrays of H/2 x W/2; pan: H x W. */
-int oracle_qnr(long H, long W, int B, const double *fused, const double *const *ms,
-               const double *pan, long win, double *qnr, double *d_lambda, double *d_s) {
+ * fused: B x H x W (ftype); ms: B arrays of H/2 x W/2 (mtype); pan: H x W (ptype). */
+int oracle_qnr_t(long H, long W, int B, const void *fused, int ftype, const void *const *ms,
+                 int mtype, const void *pan, int ptype, long win, double *qnr, double *d_lambda,
+                 double *d_s) {
     const long H2 = H / 2, W2 = W / 2, n = H * W;
     if (H / win < 1 || W / win < 1 || H2 / win < 1 || W2 / win < 1 || B < 1) return 1;
     double *pan_lo = (double *)malloc(sizeof(double) * H2 * W2);
     if (!pan_lo) return 2;
     for (long i = 0; i < H2; ++i)
         for (long j = 0; j < W2; ++j)
-            pan_lo[i * W2 + j] = (pan[(2 * i) * W + 2 * j] + pan[(2 * i) * W + 2 * j + 1] +
-                                  pan[(2 * i + 1) * W + 2 * j] + pan[(2 * i + 1) * W + 2 * j + 1]) /
-                                 4.0;
+            pan_lo[i * W2 + j] =
+                (img_at(pan, ptype, (2 * i) * W + 2 * j) + img_at(pan, ptype, (2 * i) * W + 2 * j + 1) +
+                 img_at(pan, ptype, (2 * i + 1) * W + 2 * j) +
+                 img_at(pan, ptype, (2 * i + 1) * W + 2 * j + 1)) /
+                4.0;
     double dl = 0.0;
     if (B > 1) {
         for (int l = 0; l < B; ++l)
             for (int r = 0; r < B; ++r) {
                 if (l == r) continue;
-                const double qf = oracle_q_index(H, W, fused + (long)l * n, fused + (long)r * n, win);
-                const double qm = oracle_q_index(H2, W2, ms[l], ms[r], win);
+                const double qf = oracle_q_index_t(H, W, img_plane(fused, ftype, (long)l * n), ftype,
+                                                   img_plane(fused, ftype, (long)r * n), ftype, win);
+                const double qm = oracle_q_index_t(H2, W2, ms[l], mtype, ms[r], mtype, win);
                 dl += fabs(qf - qm);
             }
         dl /= (double)(B * (B - 1));
     }
     double ds = 0.0;
     for (int l = 0; l < B; ++l) {
-        const double qf = oracle_q_index(H, W, fused + (long)l * n, pan, win);
-        const double qm = oracle_q_index(H2, W2, ms[l], pan_lo, win);
+        const double qf =
+            oracle_q_index_t(H, W, img_plane(fused, ftype, (long)l * n), ftype, pan, ptype, win);
+        const double qm = oracle_q_index_t(H2, W2, ms[l], mtype, pan_lo, ORACLE_F64, win);
         ds += fabs(qf - qm);
     }
     ds /= (double)B;
@@ -563,6 +598,12 @@ int oracle_qnr(long H, long W, int B, const double *fused, const double *const *
     *d_s = ds;
     *qnr = (1.0 - dl) * (1.0 - ds);
     return 0;
+}
+
+int oracle_qnr(long H, long W, int B, const double *fused, const double *const *ms,
+               const double *pan, long win, double *qnr, double *d_lambda, double *d_s) {
+    return oracle_qnr_t(H, W, B, fused, ORACLE_F64, (const void *const *)ms, ORACLE_F64, pan,
+                        ORACLE_F64, win, qnr, d_lambda, d_s);
 }
 
 /* ------------------------------------------------------------ threads */

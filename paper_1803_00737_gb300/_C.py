@@ -63,6 +63,14 @@ _SIGS = {
     "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
     "dwtfuse_set_rows_per_item": (_i, [_i]),
     "dwtfuse_fuse_batched_noalloc": (_i, [ctypes.POINTER(Scene), _i, _i, _i, _vp]),
+    "dwtfuse_metrics_workspace_size": (_sz, []),
+    "dwtfuse_metrics": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
+                             _vp, _vp]),
+    "dwtfuse_ergas": (_i, [_vp, _i, ctypes.POINTER(_vp), _i, _i, _i64, _i64, _vp, _sz,
+                           ctypes.POINTER(ctypes.c_double), _vp]),
+    "dwtfuse_qnr": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
+                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), _vp]),
 }
 
 _lock = threading.Lock()
@@ -200,6 +208,55 @@ def dwtfuse_fuse_batched_noalloc(scenes: list[Scene], rows_per_item: int = 0,
     st = lib().dwtfuse_fuse_batched_noalloc(arr, len(scenes), int(rows_per_item),
                                             int(blocks_per_sm), _stream(stream))
     _check(st, "dwtfuse_fuse_batched_noalloc")
+
+
+def dwtfuse_metrics_workspace_size() -> int:
+    return int(lib().dwtfuse_metrics_workspace_size())
+
+
+def _metric_args(fused: torch.Tensor, ms):
+    bands = _bands(ms)
+    B, H, W = fused.shape
+    if len(bands) != B:
+        raise ValueError("one MS band per fused band")
+    ptrs = (_vp * B)(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
+    return bands, B, H, W, ptrs
+
+
+def dwtfuse_metrics(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch.Tensor,
+                    out_device: torch.Tensor, window: int = 32, stream=None) -> None:
+    """ERGAS, QNR, D_lambda, D_s into the float64 CUDA tensor out_device[0:4] (async)."""
+    bands, B, H, W, ptrs = _metric_args(fused, ms)
+    if out_device.dtype != torch.float64 or out_device.numel() < 4:
+        raise ValueError("out_device must be a float64 CUDA tensor with >= 4 elements")
+    st = lib().dwtfuse_metrics(_dev(fused, "fused"), _dtype_code(fused, "fused"), ptrs,
+                               _dev(pan, "pan"), _dtype_code(pan, "pan"), B, H, W, int(window),
+                               _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
+                               _dev(out_device, "out_device"), _stream(stream))
+    _check(st, "dwtfuse_metrics")
+
+
+def dwtfuse_ergas(fused: torch.Tensor, ms, workspace: torch.Tensor, stream=None) -> float:
+    bands, B, H, W, ptrs = _metric_args(fused, ms)
+    out = ctypes.c_double()
+    st = lib().dwtfuse_ergas(_dev(fused, "fused"), _dtype_code(fused, "fused"), ptrs,
+                             _dtype_code(bands[0], "ms"), B, H, W, _dev(workspace, "workspace"),
+                             workspace.numel() * workspace.element_size(), ctypes.byref(out),
+                             _stream(stream))
+    _check(st, "dwtfuse_ergas")
+    return out.value
+
+
+def dwtfuse_qnr(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch.Tensor,
+                window: int = 32, stream=None) -> tuple[float, float, float]:
+    bands, B, H, W, ptrs = _metric_args(fused, ms)
+    q, dl, ds = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib().dwtfuse_qnr(_dev(fused, "fused"), _dtype_code(fused, "fused"), ptrs, _dev(pan, "pan"),
+                           _dtype_code(pan, "pan"), B, H, W, int(window), _dev(workspace, "workspace"),
+                           workspace.numel() * workspace.element_size(), ctypes.byref(q),
+                           ctypes.byref(dl), ctypes.byref(ds), _stream(stream))
+    _check(st, "dwtfuse_qnr")
+    return q.value, dl.value, ds.value
 
 
 def dwtfuse_get_last_device_status(workspace: torch.Tensor, stream=None) -> int:

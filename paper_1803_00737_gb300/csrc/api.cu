@@ -166,6 +166,105 @@ int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W
                                             rows_per_item(), static_cast<cudaStream_t>(stream)));
 }
 
+size_t dwtfuse_metrics_workspace_size(void) { return kMetricWorkspaceBytes; }
+
+static int make_metrics(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
+                        int in_dtype, int bands, int64_t H, int64_t W, int window, bool want_q,
+                        void *workspace, size_t ws_bytes, MetricLaunch *m) {
+    if (!fused || !ms || !workspace || (want_q && !pan)) return DWTFUSE_EINVAL;
+    if ((fused_dtype != DWTFUSE_U8 && fused_dtype != DWTFUSE_F32) ||
+        (in_dtype != DWTFUSE_U8 && in_dtype != DWTFUSE_F32))
+        return DWTFUSE_EINVAL;
+    if (bands < 1) return DWTFUSE_EINVAL;
+    if (bands > kMetricMaxBands) return DWTFUSE_ESHAPE;
+    if (H < 2 || W < 2 || (H & 1) || (W & 1) || H > kMaxSide || W > kMaxSide) return DWTFUSE_ESHAPE;
+    if (want_q && (window != kMetricWindow || H / 2 < window || W / 2 < window)) return DWTFUSE_ESHAPE;
+    if (ws_bytes < kMetricWorkspaceBytes) return DWTFUSE_ENOMEM;
+    const uintptr_t fe = fused_dtype == DWTFUSE_F32 ? 4 : 1, ie = in_dtype == DWTFUSE_F32 ? 4 : 1;
+    if (!aligned(workspace, 8) || !aligned(fused, 2 * fe) || (pan && !aligned(pan, 2 * ie)))
+        return DWTFUSE_EALIGN;
+    std::memset(m, 0, sizeof *m);
+    for (int b = 0; b < bands; ++b) {
+        if (!ms[b]) return DWTFUSE_EINVAL;
+        if (!aligned(ms[b], ie)) return DWTFUSE_EALIGN;
+        m->ms[b] = ms[b];
+    }
+    m->fused = fused;
+    m->pan = pan;
+    m->H = H;
+    m->W = W;
+    m->bands = bands;
+    m->want_q = want_q;
+    m->fused_f32 = fused_dtype == DWTFUSE_F32;
+    m->in_f32 = in_dtype == DWTFUSE_F32;
+    m->a4_fused = (W % 4 == 0) && aligned(fused, 4 * fe);
+    m->a4_in = (W % 4 == 0) && (!pan || aligned(pan, 4 * ie));
+    bool a16 = (W % 16 == 0) && aligned(fused, 16) && (!pan || aligned(pan, 16));
+    bool a32 = (W % 32 == 0) && (!pan || aligned(pan, 16));
+    for (int b = 0; b < bands; ++b) {
+        a16 = a16 && aligned(ms[b], 8);
+        a32 = a32 && aligned(ms[b], 16);
+    }
+    m->a16 = a16;
+    m->a32_ms = a32;
+    m->workspace = static_cast<double *>(workspace);
+    return DWTFUSE_OK;
+}
+
+int dwtfuse_metrics(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
+                    int in_dtype, int bands, int64_t H, int64_t W, int window, void *workspace,
+                    size_t ws_bytes, double *out_device, void *stream) {
+    if (!out_device) return DWTFUSE_EINVAL;
+    if (!aligned(out_device, 8)) return DWTFUSE_EALIGN;
+    MetricLaunch m;
+    const int st = make_metrics(fused, fused_dtype, ms, pan, in_dtype, bands, H, W, window, true,
+                                workspace, ws_bytes, &m);
+    if (st != DWTFUSE_OK) return st;
+    m.result = out_device;
+    return cuda_status(launch_metrics(m, static_cast<cudaStream_t>(stream)));
+}
+
+static int metrics_to_host(const MetricLaunch &m, void *stream, double *out4) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_metrics(m, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out4, m.workspace, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+int dwtfuse_ergas(const void *fused, int fused_dtype, const void *const *ms, int in_dtype,
+                  int bands, int64_t H, int64_t W, void *workspace, size_t ws_bytes,
+                  double *out_ergas, void *stream) {
+    if (!out_ergas) return DWTFUSE_EINVAL;
+    MetricLaunch m;
+    int st = make_metrics(fused, fused_dtype, ms, nullptr, in_dtype, bands, H, W, kMetricWindow,
+                          false, workspace, ws_bytes, &m);
+    if (st != DWTFUSE_OK) return st;
+    double r[4];
+    st = metrics_to_host(m, stream, r);
+    if (st == DWTFUSE_OK) *out_ergas = r[0];
+    return st;
+}
+
+int dwtfuse_qnr(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
+                int in_dtype, int bands, int64_t H, int64_t W, int window, void *workspace,
+                size_t ws_bytes, double *out_qnr, double *out_dlambda, double *out_ds,
+                void *stream) {
+    if (!out_qnr || !out_dlambda || !out_ds) return DWTFUSE_EINVAL;
+    MetricLaunch m;
+    int st = make_metrics(fused, fused_dtype, ms, pan, in_dtype, bands, H, W, window, true,
+                          workspace, ws_bytes, &m);
+    if (st != DWTFUSE_OK) return st;
+    double r[4];
+    st = metrics_to_host(m, stream, r);
+    if (st == DWTFUSE_OK) {
+        *out_qnr = r[1];
+        *out_dlambda = r[2];
+        *out_ds = r[3];
+    }
+    return st;
+}
+
 size_t dwtfuse_batched_workspace_size(void) { return 256; }
 
 int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, size_t ws_bytes,

@@ -26,6 +26,30 @@ struct BatchTable {
 };
 static_assert(sizeof(BatchTable) + 16 <= 32764, "batched scene table exceeds the parameter limit");
 
+// Quality metrics (metrics.cu).  Workspace layout, in doubles: 8 result slots
+// (ERGAS, QNR, D_lambda, D_s, ...), then kMetricMaxCtas partial rows of
+// kMetricStride for the PAN-resolution pass and as many for the MS pass.
+constexpr int kMetricMaxCtas = 1024;
+constexpr int kMetricStride = 64;    // >= pairs + bands for 8 bands (36 + 8)
+constexpr int kMetricMaxBands = 8;
+constexpr int kMetricWindow = 32;
+constexpr size_t kMetricWorkspaceBytes = sizeof(double) * (8 + 2 * (size_t)kMetricMaxCtas * kMetricStride);
+
+struct MetricLaunch {
+    const void *fused;
+    const void *ms[kMaxBands];
+    const void *pan;
+    int64_t H, W;
+    int32_t bands;
+    int32_t want_q;
+    int32_t fused_f32, in_f32;
+    int32_t a4_fused, a4_in;
+    int32_t a16;        // uint8 PAN-pass fast path: W % 16 == 0, fused/PAN 16-byte, MS 8-byte aligned
+    int32_t a32_ms;     // uint8 MS-pass fast path: W % 32 == 0, PAN and MS 16-byte aligned
+    double *workspace;  // kMetricWorkspaceBytes, 8-byte aligned
+    double *result;     // device pointer for the 4 results, or nullptr
+};
+
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);
 // SM count of the current device (cached per device).
@@ -34,6 +58,7 @@ cudaError_t sm_count(int *out);
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream);
 cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
                                  float *gpan, float *const *gms, int R, cudaStream_t stream);
+cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream);
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);
 

@@ -1,0 +1,955 @@
+// Quality metrics of the fused product (the paper reports ERGAS and QNR,
+// Sec. 4 / Table 3, without defining them; definitions used here):
+//   ERGAS = 100 * (1/2) * sqrt( (1/B) sum_b RMSE_b^2 / mu_b^2 ), reference MS_b
+//           repeated 2x2 to PAN size, mu_b its mean, RMSE over all H x W pixels.
+//   Q     = Wang-Bovik index 4 s_xy mu_x mu_y / ((s_x^2 + s_y^2)(mu_x^2 + mu_y^2))
+//           on non-overlapping 32 x 32 windows at each image's own resolution
+//           (ragged right/bottom edge dropped), averaged over windows; a zero
+//           denominator gives 1 for identical windows, 0 otherwise.
+//   D_lambda = mean over ordered band pairs |Q(F_l, F_r) - Q(MS_l, MS_r)|,
+//   D_s      = mean over bands |Q(F_l, PAN) - Q(MS_l, PAN~)|, PAN~ = 2x2 block mean,
+//   QNR      = (1 - D_lambda)(1 - D_s).
+//
+// Two passes over strips of 128 columns x 32 rows (four windows side by side,
+// one warp each): the PAN-resolution pass reads the fused bands, PAN and MS
+// (ERGAS squared errors, window sums of F_l, F_l^2, F_l F_r, F_l PAN); the
+// MS-resolution pass reads MS and PAN (window sums against PAN~, and the MS
+// means).  Every lane keeps all bands of its 4 pixels in registers, so the
+// O(B^2) cross sums are register FMAs.
+//
+// Precision without FP64 in the pixel loop (FP64 is a narrow pipe on this
+// GPU): values are shifted by 128.  For 8-bit data every window sum is an
+// exact integer (FP32 up to 2^24 in the PAN pass; int32 in the MS pass, where
+// PAN~ is carried as 4 * PAN~, an integer), the numerators n*Sxy - Sx*Sy and
+// n*Sxx - Sx^2 are formed exactly in int64, and only the final ratio is FP32
+// (relative error ~5e-7 per window).  Float data sum in FP32 and form the
+// numerators in FP64.  Per-window Q values are accumulated in FP64 in shared
+// memory; per-CTA partials go to the caller's workspace and a one-CTA kernel
+// reduces them in a fixed order (deterministic).
+#include <type_traits>
+
+#include "fuse_tile.cuh"
+#include "launch.h"
+
+namespace dwtfuse {
+
+namespace {
+
+constexpr int kMThreads = 256;
+constexpr int kMWarps = kMThreads / 32;
+constexpr int kWin = 32;
+constexpr float kShift = 128.0f;
+
+template <int NB>
+struct Pairs {
+    static constexpr int K = NB + 1;                 // images: NB bands + the PAN image
+    static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs, then band-PAN pairs
+};
+
+__device__ __forceinline__ void load4f(const uint8_t *p, bool a4, bool two, float *v) {
+    if (a4) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(p));
+        v[0] = byte_f(w, 0); v[1] = byte_f(w, 1); v[2] = byte_f(w, 2); v[3] = byte_f(w, 3);
+    } else {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned short *>(p));
+        v[0] = byte_f(w, 0); v[1] = byte_f(w, 1);
+        if (two) {
+            const uint32_t u = __ldg(reinterpret_cast<const unsigned short *>(p + 2));
+            v[2] = byte_f(u, 0); v[3] = byte_f(u, 1);
+        } else {
+            v[2] = v[3] = 0.f;
+        }
+    }
+}
+__device__ __forceinline__ void load4f(const float *p, bool a4, bool two, float *v) {
+    if (a4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(p));
+        v[0] = q.x; v[1] = q.y;
+        if (two) {
+            const float2 u = __ldg(reinterpret_cast<const float2 *>(p + 2));
+            v[2] = u.x; v[3] = u.y;
+        } else {
+            v[2] = v[3] = 0.f;
+        }
+    }
+}
+__device__ __forceinline__ float load1f(const uint8_t *p) { return (float)__ldg(p); }
+__device__ __forceinline__ float load1f(const float *p) { return __ldg(p); }
+
+constexpr int kN = kWin * kWin;  // pixels per window
+
+__device__ __forceinline__ float xor_sum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+__device__ __forceinline__ int xor_sum8(int v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
+// Window sums of one image pair: x and y are the shifted values (x = X - 128),
+// y carried as sy_scale * y (1, or 4 for PAN~ in the MS pass).
+struct WinSums {
+    double sx, sxx, sy, syy, sxy;
+};
+
+// Q of one window, given exact integer sums (8-bit data).  ys = scale of y.
+__device__ __forceinline__ float q_exact(long long sx, long long sxx, long long sy, long long syy,
+                                         long long sxy, int ys) {
+    const long long n = kN;
+    const long long vx = n * sxx - sx * sx;                 // n^2 var(x)
+    const long long vy = n * syy - sy * sy;                 // ys^2 n^2 var(y)
+    const long long cxy = n * sxy - sx * sy;                // ys n^2 cov(x, y)
+    const long long ax = sx + 128 * n;                      // n mean(X)
+    const long long ay = sy + 128 * n * ys;                 // ys n mean(Y)
+    const float inv = 1.0f / (float)ys, inv2 = inv * inv;
+    const float fvx = (float)vx, fvy = (float)vy * inv2, fc = (float)cxy * inv;
+    const float fax = (float)ax, fay = (float)ay * inv;
+    const float den = (fvx + fvy) * (fax * fax + fay * fay);
+    if (vx + vy == 0 || (ax == 0 && ay == 0)) {
+        // zero denominator: identical windows <=> sum (ys x - y)^2 = 0
+        const long long d2 = (long long)ys * ys * sxx - 2LL * ys * sxy + syy;
+        return (d2 == 0) ? 1.0f : 0.0f;
+    }
+    return 4.0f * fc * fax * fay / den;
+}
+
+// Q of one window from float sums (float data): numerators in FP64.
+__device__ __forceinline__ float q_float(float sx, float sxx, float sy, float syy, float sxy) {
+    const double n = kN;
+    const double vx = n * (double)sxx - (double)sx * (double)sx;
+    const double vy = n * (double)syy - (double)sy * (double)sy;
+    const double cxy = n * (double)sxy - (double)sx * (double)sy;
+    const double ax = (double)sx + 128.0 * n, ay = (double)sy + 128.0 * n;
+    const float den = (float)(vx + vy) * ((float)ax * (float)ax + (float)ay * (float)ay);
+    if (den == 0.0f) {
+        const double d2 = (double)sxx - 2.0 * (double)sxy + (double)syy;
+        return (d2 == 0.0 && sx == sy) ? 1.0f : 0.0f;
+    }
+    return 4.0f * (float)cxy * (float)ax * (float)ay / den;
+}
+
+// Cross sums of one pixel: band-band pairs (b < c), then band-PAN pairs.
+template <int NB, typename A>
+__device__ __forceinline__ void accumulate_pixel(const A *v, A *s1, A *s2, A *sxy) {
+#pragma unroll
+    for (int k = 0; k <= NB; ++k) {
+        s1[k] += v[k];
+        s2[k] += v[k] * v[k];
+    }
+    int idx = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] += v[b] * v[c];
+#pragma unroll
+    for (int b = 0; b < NB; ++b, ++idx) sxy[idx] += v[b] * v[NB];
+}
+
+// After a strip: window sums over the 8 lanes of each window (every lane of
+// the warp takes part), Q per pair on every lane, and the first lane of each
+// full window adds its Q values to its shared slot.  `exact`: sums are exact
+// integers; ys: scale of the last image (PAN or 4 * PAN~).
+template <int NB, typename A>
+__device__ __forceinline__ void finish_strip(const A *s1, const A *s2, const A *sxy, bool exact,
+                                             int ys, bool leader, double *slot) {
+    constexpr int K = NB + 1;
+    A S1[K], S2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        S1[k] = xor_sum8(s1[k]);
+        S2[k] = xor_sum8(s2[k]);
+    }
+    int idx = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+        for (int c = b + 1; c <= NB; ++c) {
+            // pairs in the order of accumulate_pixel: band-band first, then band-PAN
+            const int p = (c < NB) ? idx : -1;
+            if (c < NB) ++idx;
+            if (p < 0) continue;
+            const A Sxy = xor_sum8(sxy[p]);
+            const float q = exact ? q_exact((long long)S1[b], (long long)S2[b], (long long)S1[c],
+                                            (long long)S2[c], (long long)Sxy, 1)
+                                  : q_float((float)S1[b], (float)S2[b], (float)S1[c], (float)S2[c], (float)Sxy);
+            if (leader) slot[p] += (double)q;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b, ++idx) {
+        const A Sxy = xor_sum8(sxy[idx]);
+        const float q = exact ? q_exact((long long)S1[b], (long long)S2[b], (long long)S1[NB],
+                                        (long long)S2[NB], (long long)Sxy, ys)
+                              : q_float((float)S1[b], (float)S2[b], (float)S1[NB], (float)S2[NB], (float)Sxy);
+        if (leader) slot[idx] += (double)q;
+    }
+}
+
+struct MetricArgs {
+    const void *fused;             // [B][H][W], TF
+    const void *ms[kMaxBands];     // (H/2) x (W/2), TI
+    const void *pan;               // H x W, TI (may be null when want_q == 0)
+    double *partial;               // [gridDim][stride] per pass
+    int64_t H, W;
+    int32_t bands;
+    int32_t want_q;
+    int32_t a4_fused, a4_in;       // 4-pixel vector path allowed
+    int32_t stride;                // doubles per CTA partial row
+    int32_t pad_;
+};
+
+// --------------------------------------------------------------- PAN-resolution pass
+
+template <typename TF, typename TI, int NB>
+__global__ void __launch_bounds__(kMThreads, 2)
+metrics_pan_kernel(const __grid_constant__ MetricArgs a) {
+    constexpr int K = Pairs<NB>::K, P = Pairs<NB>::P;
+    // 8-bit data: shifted values are integers and every per-lane (<= 2^21) and
+    // window (<= 2^24) sum is exact in FP32.
+    constexpr bool kExact = std::is_same<TF, uint8_t>::value && std::is_same<TI, uint8_t>::value;
+    __shared__ double sq[kMWarps][4][P];  // one slot per window of each warp's strip
+    __shared__ double sse[kMWarps][NB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t H = a.H, W = a.W, W2 = W >> 1, HW = H * W;
+    for (int k = lane; k < 4 * P; k += 32) sq[warp][k / P][k % P] = 0.0;
+    double se_tot[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) se_tot[b] = 0.0;
+    const TF *F = static_cast<const TF *>(a.fused);
+    const TI *pan = static_cast<const TI *>(a.pan);
+    const int64_t sx_n = (W + kWarpCols - 1) / kWarpCols, sy_n = (H + kWin - 1) / kWin;
+    const int64_t items = sx_n * sy_n;
+    const int64_t nw = (int64_t)gridDim.x * kMWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kMWarps + warp; it < items; it += nw) {
+        const int64_t x = (it % sx_n) * kWarpCols + 4 * lane;
+        const int64_t y0 = (it / sx_n) * kWin;
+        const bool act = x < W, two = x + 2 < W;
+        const int64_t xl = act ? x : 0;
+        const int64_t xwin = x - 4 * (lane & 7);  // first column of this lane's window
+        const bool full = a.want_q && (y0 + kWin <= H) && (xwin + kWin <= W);
+        const int64_t y1 = min(y0 + (int64_t)kWin, H);
+        float s1[K], s2[K], sxy[P], se[NB];
+#pragma unroll
+        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) sxy[k] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se[b] = 0.f;
+        for (int64_t y = y0; y < y1; ++y) {
+            float f[NB][4], m[NB][2];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                load4f(F + (int64_t)b * HW + y * W + xl, a.a4_fused != 0, two, f[b]);
+                const TI *mr = static_cast<const TI *>(a.ms[b]) + (y >> 1) * W2 + (xl >> 1);
+                m[b][0] = load1f(mr);
+                m[b][1] = two ? load1f(mr + 1) : 0.f;
+            }
+            float p[4];
+            if (full) load4f(pan + y * W + xl, a.a4_in != 0, true, p);
+            if (!act) continue;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float d = (q < 2 || two) ? f[b][q] - m[b][q >> 1] : 0.f;
+                    se[b] = fmaf(d, d, se[b]);
+                }
+            }
+            if (full) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[K];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) v[b] = f[b][q] - kShift;
+                    v[NB] = p[q] - kShift;
+                    accumulate_pixel<NB>(v, s1, s2, sxy);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se_tot[b] += (double)se[b];
+        if (!__any_sync(0xffffffffu, full)) continue;
+        finish_strip<NB, float>(s1, s2, sxy, kExact, 1, full && (lane & 7) == 0, sq[warp][lane >> 3]);
+    }
+    // Per-warp squared errors, then the CTA's partial row.
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        double v = se_tot[b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sse[warp][b] = v;
+    }
+    __syncthreads();
+    double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    for (int k = threadIdx.x; k < P + NB; k += kMThreads) {
+        double acc = 0.0;
+        for (int w = 0; w < kMWarps; ++w)
+            acc += k < P ? ((sq[w][0][k] + sq[w][1][k]) + (sq[w][2][k] + sq[w][3][k])) : sse[w][k - P];
+        out[k] = acc;
+    }
+}
+
+// --------------------------------------------------------------- 8-bit fast paths
+
+// Asynchronous global -> shared copies (the per-warp row ring below).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// 8-bit product and inputs, W % 16 == 0, 16-byte aligned planes (8 for MS).
+// A lane owns 16 consecutive pixels of a row, a window is two lanes, a warp
+// strip is 512 columns (16 windows) x 32 rows.  Each lane streams its rows
+// through a private ring of kStages rows in shared memory with cp.async, so
+// several rows of every band are in flight without holding registers; it
+// reads back only the bytes it copied, so no barrier is needed.  Shifted
+// values are signed bytes (X ^ 0x80 = X - 128) and every sum is a dp4a over 4
+// pixels, exact in int32.
+constexpr int kLanePx = 16;
+constexpr int kStrip = 32 * kLanePx;
+constexpr int kWinPerStrip = kStrip / kWin;
+constexpr int kFastWarps = 8;
+
+template <int NB>
+struct FastPan {
+    static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
+    static constexpr int kStages = NB <= 6 ? 4 : 3;
+    static constexpr int kRowBytes = K * 512 + NB * 256;  // per warp: F bands + PAN (16 B/lane), MS (8 B/lane)
+    static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
+                                 kFastWarps * NB * 8;
+};
+
+template <int NB>
+__global__ void __launch_bounds__(kFastWarps * 32, 1)
+metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
+    using C = FastPan<NB>;
+    constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *ring = smem + warp * S * RB;
+    float *sq = reinterpret_cast<float *>(smem + kFastWarps * S * RB) + warp * kWinPerStrip * P;
+    double *sse = reinterpret_cast<double *>(smem + kFastWarps * S * RB + kFastWarps * kWinPerStrip * P * 4);
+    for (int k = lane; k < kWinPerStrip * P; k += 32) sq[k] = 0.f;
+    double se_tot[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) se_tot[b] = 0.0;
+    const int64_t H = a.H, W = a.W, W2 = W >> 1, HW = H * W;
+    const uint8_t *F = static_cast<const uint8_t *>(a.fused);
+    const uint8_t *pan = static_cast<const uint8_t *>(a.pan);
+    const int64_t sx_n = (W + kStrip - 1) / kStrip, sy_n = (H + kWin - 1) / kWin;
+    const int64_t items = sx_n * sy_n;
+    const int64_t nw = (int64_t)gridDim.x * kFastWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
+        const int64_t x = (it % sx_n) * kStrip + kLanePx * lane;
+        const int64_t y0 = (it / sx_n) * kWin;
+        const bool act = x < W;
+        const int64_t xwin = x - kLanePx * (lane & 1);
+        const bool full = a.want_q && (y0 + kWin <= H) && (xwin + kWin <= W);
+        const int nrows = (int)min((int64_t)kWin, H - y0);
+        // Row r of this strip into ring slot r % S (only this lane's bytes).
+        auto issue = [&](int r) {
+            if (r < nrows && act) {
+                unsigned char *slot = ring + (r % S) * RB;
+                const int64_t y = y0 + r;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    cp_async16(slot + b * 512 + lane * 16, F + (int64_t)b * HW + y * W + x);
+                if (a.want_q) cp_async16(slot + NB * 512 + lane * 16, pan + y * W + x);
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    cp_async8(slot + K * 512 + b * 256 + lane * 8,
+                              static_cast<const uint8_t *>(a.ms[b]) + (y >> 1) * W2 + (x >> 1));
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int r = 0; r < S - 1; ++r) issue(r);
+        int s1[K], s2[K], sxy[P], se[NB];
+#pragma unroll
+        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) sxy[k] = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se[b] = 0;
+        for (int r = 0; r < nrows; ++r) {
+            issue(r + S - 1);
+            cp_async_wait<S - 1>();
+            if (!act) continue;
+            const unsigned char *slot = ring + (r % S) * RB;
+            uint4 f[NB];
+            uint2 m[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                f[b] = *reinterpret_cast<const uint4 *>(slot + b * 512 + lane * 16);
+                m[b] = *reinterpret_cast<const uint2 *>(slot + K * 512 + b * 256 + lane * 8);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const uint32_t fw = q == 0 ? f[b].x : q == 1 ? f[b].y : q == 2 ? f[b].z : f[b].w;
+                    const uint32_t mw = q < 2 ? m[b].x : m[b].y;
+                    // MS pixels 2q, 2q+1 of this lane, each repeated twice
+                    const uint32_t rep = __byte_perm(mw, 0u, (q & 1) ? 0x3322u : 0x1100u);
+                    const uint32_t d = __vabsdiffu4(fw, rep);
+                    se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
+                }
+            }
+            if (full) {
+                const uint4 pw = *reinterpret_cast<const uint4 *>(slot + NB * 512 + lane * 16);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int v[K];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        v[b] = (int)((q == 0 ? f[b].x : q == 1 ? f[b].y : q == 2 ? f[b].z : f[b].w) ^ 0x80808080u);
+                    v[NB] = (int)((q == 0 ? pw.x : q == 1 ? pw.y : q == 2 ? pw.z : pw.w) ^ 0x80808080u);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        s1[k] = __dp4a(v[k], 0x01010101, s1[k]);
+                        s2[k] = __dp4a(v[k], v[k], s2[k]);
+                    }
+                    int idx = 0;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b, ++idx) sxy[idx] = __dp4a(v[b], v[NB], sxy[idx]);
+                }
+            }
+        }
+        cp_async_wait<0>();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se_tot[b] += (double)(unsigned)se[b];
+        if (!__any_sync(0xffffffffu, full)) continue;
+        // Window sums over the lane pair, Q per pair on every lane; the even
+        // lane of a full window adds its Q values to its slot.
+        int S1[K], S2[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            S1[k] = s1[k] + __shfl_xor_sync(0xffffffffu, s1[k], 1);
+            S2[k] = s2[k] + __shfl_xor_sync(0xffffffffu, s2[k], 1);
+        }
+        const bool leader = full && (lane & 1) == 0;
+        float *slotq = sq + (lane >> 1) * P;
+        int idx = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = b + 1; c < NB; ++c, ++idx) {
+                const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
+                const float qv = q_exact(S1[b], S2[b], S1[c], S2[c], Sxy, 1);
+                if (leader) slotq[idx] += qv;
+            }
+#pragma unroll
+        for (int b = 0; b < NB; ++b, ++idx) {
+            const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
+            const float qv = q_exact(S1[b], S2[b], S1[NB], S2[NB], Sxy, 1);
+            if (leader) slotq[idx] += qv;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        double v = se_tot[b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sse[warp * NB + b] = v;
+    }
+    __syncthreads();
+    const float *sq0 = reinterpret_cast<const float *>(smem + kFastWarps * S * RB);
+    double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    for (int k = threadIdx.x; k < P + NB; k += kFastWarps * 32) {
+        double acc = 0.0;
+        for (int w = 0; w < kFastWarps; ++w) {
+            if (k < P) {
+                for (int s = 0; s < kWinPerStrip; ++s) acc += (double)sq0[(w * kWinPerStrip + s) * P + k];
+            } else {
+                acc += sse[w * NB + k - P];
+            }
+        }
+        out[k] = acc;
+    }
+}
+
+template <int NB>
+struct FastMs {
+    static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
+    static constexpr int kStages = NB <= 6 ? 4 : 3;
+    static constexpr int kRowBytes = NB * 512 + 4 * 512;  // per warp: MS bands (16 B/lane), 2 PAN rows (32 B/lane each)
+    static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
+                                 kFastWarps * NB * 8;
+};
+
+// MS-resolution pass, 8-bit: a lane owns 16 MS pixels of an MS row (and the
+// 2 x 32 PAN pixels above them).  MS values are signed bytes (dp4a); PAN~ is
+// carried as Z = 4 PAN~ - 512 (the 2x2 sum, exact) and its products use
+// integer multiply-adds.
+template <int NB>
+__global__ void __launch_bounds__(kFastWarps * 32, 1)
+metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
+    using C = FastMs<NB>;
+    constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *ring = smem + warp * S * RB;
+    float *sq = reinterpret_cast<float *>(smem + kFastWarps * S * RB) + warp * kWinPerStrip * P;
+    double *ssum = reinterpret_cast<double *>(smem + kFastWarps * S * RB + kFastWarps * kWinPerStrip * P * 4);
+    for (int k = lane; k < kWinPerStrip * P; k += 32) sq[k] = 0.f;
+    double sum_tot[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) sum_tot[b] = 0.0;
+    const int64_t H2 = a.H >> 1, W2 = a.W >> 1, W = a.W;
+    const uint8_t *pan = static_cast<const uint8_t *>(a.pan);
+    const int64_t sx_n = (W2 + kStrip - 1) / kStrip, sy_n = (H2 + kWin - 1) / kWin;
+    const int64_t items = sx_n * sy_n;
+    const int64_t nw = (int64_t)gridDim.x * kFastWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
+        const int64_t j = (it % sx_n) * kStrip + kLanePx * lane;  // MS column
+        const int64_t i0 = (it / sx_n) * kWin;
+        const bool act = j < W2;
+        const int64_t jwin = j - kLanePx * (lane & 1);
+        const bool full = a.want_q && (i0 + kWin <= H2) && (jwin + kWin <= W2);
+        const int nrows = (int)min((int64_t)kWin, H2 - i0);
+        auto issue = [&](int r) {
+            if (r < nrows && act) {
+                unsigned char *slot = ring + (r % S) * RB;
+                const int64_t i = i0 + r;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    cp_async16(slot + b * 512 + lane * 16, static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j);
+                if (full) {
+                    const uint8_t *p0 = pan + (2 * i) * W + 2 * j;
+                    cp_async16(slot + NB * 512 + lane * 32, p0);
+                    cp_async16(slot + NB * 512 + lane * 32 + 16, p0 + 16);
+                    cp_async16(slot + NB * 512 + 1024 + lane * 32, p0 + W);
+                    cp_async16(slot + NB * 512 + 1024 + lane * 32 + 16, p0 + W + 16);
+                }
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int r = 0; r < S - 1; ++r) issue(r);
+        int s1[K], s2[K], sxy[P], sm[NB];
+#pragma unroll
+        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) sxy[k] = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) sm[b] = 0;
+        for (int r = 0; r < nrows; ++r) {
+            issue(r + S - 1);
+            cp_async_wait<S - 1>();
+            if (!act) continue;
+            const unsigned char *slot = ring + (r % S) * RB;
+            uint4 mv[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                mv[b] = *reinterpret_cast<const uint4 *>(slot + b * 512 + lane * 16);
+                sm[b] = (int)__dp4a(mv[b].x, 0x01010101u, (unsigned)sm[b]);
+                sm[b] = (int)__dp4a(mv[b].y, 0x01010101u, (unsigned)sm[b]);
+                sm[b] = (int)__dp4a(mv[b].z, 0x01010101u, (unsigned)sm[b]);
+                sm[b] = (int)__dp4a(mv[b].w, 0x01010101u, (unsigned)sm[b]);
+            }
+            if (!full) continue;
+            const uint4 *r0 = reinterpret_cast<const uint4 *>(slot + NB * 512 + lane * 32);
+            const uint4 *r1 = reinterpret_cast<const uint4 *>(slot + NB * 512 + 1024 + lane * 32);
+            const uint4 a0 = r0[0], a1 = r0[1], b0 = r1[0], b1 = r1[1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // PAN words of rows 2i, 2i+1 covering MS pixels 4q .. 4q+3
+                const uint32_t ua = q == 0 ? a0.x : q == 1 ? a0.z : q == 2 ? a1.x : a1.z;
+                const uint32_t ub = q == 0 ? a0.y : q == 1 ? a0.w : q == 2 ? a1.y : a1.w;
+                const uint32_t la = q == 0 ? b0.x : q == 1 ? b0.z : q == 2 ? b1.x : b1.z;
+                const uint32_t lb = q == 0 ? b0.y : q == 1 ? b0.w : q == 2 ? b1.y : b1.w;
+                int z[4];
+                z[0] = (int)__dp4a(__byte_perm(ua, la, 0x5410u), 0x01010101u, 0u) - 512;
+                z[1] = (int)__dp4a(__byte_perm(ua, la, 0x7632u), 0x01010101u, 0u) - 512;
+                z[2] = (int)__dp4a(__byte_perm(ub, lb, 0x5410u), 0x01010101u, 0u) - 512;
+                z[3] = (int)__dp4a(__byte_perm(ub, lb, 0x7632u), 0x01010101u, 0u) - 512;
+                int v[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    v[b] = (int)((q == 0 ? mv[b].x : q == 1 ? mv[b].y : q == 2 ? mv[b].z : mv[b].w) ^ 0x80808080u);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    s1[b] = __dp4a(v[b], 0x01010101, s1[b]);
+                    s2[b] = __dp4a(v[b], v[b], s2[b]);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    s1[NB] += z[t];
+                    s2[NB] += z[t] * z[t];
+                }
+                int idx = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+#pragma unroll
+                for (int b = 0; b < NB; ++b, ++idx) {
+                    // signed bytes of v[b] times Z
+                    const int w = v[b];
+                    sxy[idx] += ((w << 24) >> 24) * z[0] + ((w << 16) >> 24) * z[1] +
+                                ((w << 8) >> 24) * z[2] + (w >> 24) * z[3];
+                }
+            }
+        }
+        cp_async_wait<0>();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) sum_tot[b] += (double)(unsigned)sm[b];
+        if (!__any_sync(0xffffffffu, full)) continue;
+        int S1[K], S2[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            S1[k] = s1[k] + __shfl_xor_sync(0xffffffffu, s1[k], 1);
+            S2[k] = s2[k] + __shfl_xor_sync(0xffffffffu, s2[k], 1);
+        }
+        const bool leader = full && (lane & 1) == 0;
+        float *slotq = sq + (lane >> 1) * P;
+        int idx = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int c = b + 1; c < NB; ++c, ++idx) {
+                const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
+                const float qv = q_exact(S1[b], S2[b], S1[c], S2[c], Sxy, 1);
+                if (leader) slotq[idx] += qv;
+            }
+#pragma unroll
+        for (int b = 0; b < NB; ++b, ++idx) {
+            const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
+            const float qv = q_exact(S1[b], S2[b], S1[NB], S2[NB], Sxy, 4);
+            if (leader) slotq[idx] += qv;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        double v = sum_tot[b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) ssum[warp * NB + b] = v;
+    }
+    __syncthreads();
+    const float *sq0 = reinterpret_cast<const float *>(smem + kFastWarps * S * RB);
+    double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    for (int k = threadIdx.x; k < P + NB; k += kFastWarps * 32) {
+        double acc = 0.0;
+        for (int w = 0; w < kFastWarps; ++w) {
+            if (k < P) {
+                for (int s = 0; s < kWinPerStrip; ++s) acc += (double)sq0[(w * kWinPerStrip + s) * P + k];
+            } else {
+                acc += ssum[w * NB + k - P];
+            }
+        }
+        out[k] = acc;
+    }
+}
+
+// --------------------------------------------------------------- MS-resolution pass
+
+template <typename TI, int NB>
+__global__ void __launch_bounds__(kMThreads, 2)
+metrics_ms_kernel(const __grid_constant__ MetricArgs a) {
+    constexpr int K = Pairs<NB>::K, P = Pairs<NB>::P;
+    // 8-bit data: integer accumulation, PAN~ carried as 4 * (PAN~ - 128).
+    constexpr bool kExact = std::is_same<TI, uint8_t>::value;
+    using Acc = typename std::conditional<kExact, int, float>::type;
+    __shared__ double sq[kMWarps][4][P];
+    __shared__ double ssum[kMWarps][NB];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t H2 = a.H >> 1, W2 = a.W >> 1, W = a.W;
+    for (int k = lane; k < 4 * P; k += 32) sq[warp][k / P][k % P] = 0.0;
+    double sum_tot[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) sum_tot[b] = 0.0;
+    const TI *pan = static_cast<const TI *>(a.pan);
+    const int64_t sx_n = (W2 + kWarpCols - 1) / kWarpCols, sy_n = (H2 + kWin - 1) / kWin;
+    const int64_t items = sx_n * sy_n;
+    const int64_t nw = (int64_t)gridDim.x * kMWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kMWarps + warp; it < items; it += nw) {
+        const int64_t j = (it % sx_n) * kWarpCols + 4 * lane;  // MS column
+        const int64_t i0 = (it / sx_n) * kWin;
+        const int64_t jwin = j - 4 * (lane & 7);
+        const bool full = a.want_q && (i0 + kWin <= H2) && (jwin + kWin <= W2);
+        const int64_t i1 = min(i0 + (int64_t)kWin, H2);
+        Acc s1[K], s2[K], sxy[P];
+        float sm[NB];
+#pragma unroll
+        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) sxy[k] = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) sm[b] = 0.f;
+        for (int64_t i = i0; i < i1; ++i) {
+            float v4[NB][4];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const TI *mr = static_cast<const TI *>(a.ms[b]) + i * W2;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v4[b][q] = (j + q < W2) ? load1f(mr + j + q) : 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sm[b] += v4[b][q];
+            }
+            if (full) {
+                // PAN~ from PAN rows 2i, 2i+1, columns 2j .. 2j+7.
+                float r0[8], r1[8];
+                load4f(pan + (2 * i) * W + 2 * j, a.a4_in != 0, true, r0);
+                load4f(pan + (2 * i) * W + 2 * j + 4, a.a4_in != 0, true, r0 + 4);
+                load4f(pan + (2 * i + 1) * W + 2 * j, a.a4_in != 0, true, r1);
+                load4f(pan + (2 * i + 1) * W + 2 * j + 4, a.a4_in != 0, true, r1 + 4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float s4 = (r0[2 * q] + r0[2 * q + 1]) + (r1[2 * q] + r1[2 * q + 1]);
+                    Acc v[K];
+                    if (kExact) {
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) v[b] = (Acc)(v4[b][q] - kShift);
+                        v[NB] = (Acc)(s4 - 4.0f * kShift);  // 4 * (PAN~ - 128), exact
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) v[b] = (Acc)(v4[b][q] - kShift);
+                        v[NB] = (Acc)(s4 * 0.25f - kShift);
+                    }
+                    accumulate_pixel<NB, Acc>(v, s1, s2, sxy);
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) sum_tot[b] += (double)sm[b];
+        if (!__any_sync(0xffffffffu, full)) continue;
+        finish_strip<NB, Acc>(s1, s2, sxy, kExact, kExact ? 4 : 1, full && (lane & 7) == 0,
+                              sq[warp][lane >> 3]);
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        double v = sum_tot[b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) ssum[warp][b] = v;
+    }
+    __syncthreads();
+    double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    for (int k = threadIdx.x; k < P + NB; k += kMThreads) {
+        double acc = 0.0;
+        for (int w = 0; w < kMWarps; ++w)
+            acc += k < P ? ((sq[w][0][k] + sq[w][1][k]) + (sq[w][2][k] + sq[w][3][k])) : ssum[w][k - P];
+        out[k] = acc;
+    }
+}
+
+// --------------------------------------------------------------- finalize
+
+// One CTA: sums the per-CTA partial rows in a fixed order and writes
+// out[0..3] = ERGAS, QNR, D_lambda, D_s (QNR terms NaN when not requested or
+// when no full window exists at either resolution).
+__global__ void __launch_bounds__(256)
+metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, int ctas_ms,
+                        int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
+                        int64_t nwin_ms, double *out) {
+    __shared__ double tot_pan[64 + kMaxBands];
+    __shared__ double tot_ms[64 + kMaxBands];
+    const int P = nb * (nb - 1) / 2 + nb;
+    for (int k = threadIdx.x; k < P + nb; k += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int c = 0; c < ctas_pan; ++c) a += pan_part[(int64_t)c * stride + k];
+        for (int c = 0; c < ctas_ms; ++c) b += ms_part[(int64_t)c * stride + k];
+        tot_pan[k] = a;
+        tot_ms[k] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double n = (double)H * (double)W, nms = (double)(H / 2) * (double)(W / 2);
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double mse = tot_pan[P + b] / n, mu = tot_ms[P + b] / nms;
+        acc += mse / (mu * mu);
+    }
+    out[0] = 100.0 * 0.5 * sqrt(acc / nb);
+    if (!want_q || nwin_pan < 1 || nwin_ms < 1) {
+        out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    double dl = 0.0;
+    int idx = 0;
+    for (int b = 0; b < nb; ++b)
+        for (int c = b + 1; c < nb; ++c, ++idx)
+            dl += fabs(tot_pan[idx] / nwin_pan - tot_ms[idx] / nwin_ms);
+    dl = nb > 1 ? 2.0 * dl / (nb * (nb - 1)) : 0.0;
+    double ds = 0.0;
+    for (int b = 0; b < nb; ++b, ++idx) ds += fabs(tot_pan[idx] / nwin_pan - tot_ms[idx] / nwin_ms);
+    ds /= nb;
+    out[1] = (1.0 - dl) * (1.0 - ds);
+    out[2] = dl;
+    out[3] = ds;
+}
+
+template <typename TF, typename TI, int NB>
+const void *pan_fn() { return reinterpret_cast<const void *>(&metrics_pan_kernel<TF, TI, NB>); }
+template <typename TI, int NB>
+const void *ms_fn() { return reinterpret_cast<const void *>(&metrics_ms_kernel<TI, NB>); }
+
+template <typename TF, typename TI>
+const void *pan_fn_nb(int nb) {
+    switch (nb) {
+        case 1: return pan_fn<TF, TI, 1>();
+        case 2: return pan_fn<TF, TI, 2>();
+        case 3: return pan_fn<TF, TI, 3>();
+        case 4: return pan_fn<TF, TI, 4>();
+        case 5: return pan_fn<TF, TI, 5>();
+        case 6: return pan_fn<TF, TI, 6>();
+        case 7: return pan_fn<TF, TI, 7>();
+        default: return pan_fn<TF, TI, 8>();
+    }
+}
+struct FastFn {
+    const void *fn;
+    int smem;
+};
+template <int NB>
+FastFn pan_u8_fn() { return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB>), FastPan<NB>::kSmem}; }
+template <int NB>
+FastFn ms_u8_fn() { return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB>), FastMs<NB>::kSmem}; }
+FastFn fast_fn(bool ms_pass, int nb) {
+    switch (nb) {
+        case 1: return ms_pass ? ms_u8_fn<1>() : pan_u8_fn<1>();
+        case 2: return ms_pass ? ms_u8_fn<2>() : pan_u8_fn<2>();
+        case 3: return ms_pass ? ms_u8_fn<3>() : pan_u8_fn<3>();
+        case 4: return ms_pass ? ms_u8_fn<4>() : pan_u8_fn<4>();
+        case 5: return ms_pass ? ms_u8_fn<5>() : pan_u8_fn<5>();
+        case 6: return ms_pass ? ms_u8_fn<6>() : pan_u8_fn<6>();
+        case 7: return ms_pass ? ms_u8_fn<7>() : pan_u8_fn<7>();
+        default: return ms_pass ? ms_u8_fn<8>() : pan_u8_fn<8>();
+    }
+}
+
+// Grid of a fast-path kernel: one 256-thread CTA per SM (the row rings use
+// most of shared memory), at most kMetricMaxCtas.
+cudaError_t fast_grid(const FastFn &f, int64_t items, int *grid) {
+    static_assert(kMetricMaxCtas >= 1, "");
+    cudaError_t e = cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f.fn, kFastWarps * 32, f.smem);
+    if (e != cudaSuccess) return e;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t g = (items + kFastWarps - 1) / kFastWarps;
+    const int64_t cap = (int64_t)sms * occ;
+    if (g > cap) g = cap;
+    if (g > kMetricMaxCtas) g = kMetricMaxCtas;
+    if (g < 1) g = 1;
+    *grid = (int)g;
+    return cudaSuccess;
+}
+
+template <typename TI>
+const void *ms_fn_nb(int nb) {
+    switch (nb) {
+        case 1: return ms_fn<TI, 1>();
+        case 2: return ms_fn<TI, 2>();
+        case 3: return ms_fn<TI, 3>();
+        case 4: return ms_fn<TI, 4>();
+        case 5: return ms_fn<TI, 5>();
+        case 6: return ms_fn<TI, 6>();
+        case 7: return ms_fn<TI, 7>();
+        default: return ms_fn<TI, 8>();
+    }
+}
+
+cudaError_t grid_for(const void *fn, int64_t items, int *grid) {
+    int occ = 0, sms = 0;
+    cudaError_t e = resident_blocks(fn, kMThreads, &occ);
+    if (e != cudaSuccess) return e;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    int64_t g = (items + kMWarps - 1) / kMWarps;
+    const int64_t cap = (int64_t)sms * occ;
+    if (g > cap) g = cap;
+    if (g > kMetricMaxCtas) g = kMetricMaxCtas;
+    if (g < 1) g = 1;
+    *grid = (int)g;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
+    MetricArgs a{};
+    a.fused = m.fused;
+    for (int b = 0; b < m.bands; ++b) a.ms[b] = m.ms[b];
+    a.pan = m.pan;
+    a.H = m.H;
+    a.W = m.W;
+    a.bands = m.bands;
+    a.want_q = m.want_q;
+    a.a4_fused = m.a4_fused;
+    a.a4_in = m.a4_in;
+    a.stride = kMetricStride;
+    const bool fast = !m.fused_f32 && !m.in_f32 && m.a16;
+    double *out = m.workspace;
+    double *pan_part = m.workspace + 8;
+    double *ms_part = pan_part + (int64_t)kMetricMaxCtas * kMetricStride;
+    int gp = 0, gm = 0;
+    cudaError_t e;
+    // PAN-resolution pass
+    if (fast) {
+        const FastFn fp = fast_fn(false, m.bands);
+        const int64_t items = ((m.W + kStrip - 1) / kStrip) * ((m.H + kWin - 1) / kWin);
+        e = fast_grid(fp, items, &gp);
+        if (e != cudaSuccess) return e;
+        a.partial = pan_part;
+        void *args[] = {&a};
+        e = cudaLaunchKernel(fp.fn, dim3(gp), dim3(kFastWarps * 32), args, fp.smem, stream);
+    } else {
+        const void *fp = m.fused_f32 ? (m.in_f32 ? pan_fn_nb<float, float>(m.bands) : pan_fn_nb<float, uint8_t>(m.bands))
+                                     : (m.in_f32 ? pan_fn_nb<uint8_t, float>(m.bands) : pan_fn_nb<uint8_t, uint8_t>(m.bands));
+        const int64_t items = ((m.W + kWarpCols - 1) / kWarpCols) * ((m.H + kWin - 1) / kWin);
+        e = grid_for(fp, items, &gp);
+        if (e != cudaSuccess) return e;
+        a.partial = pan_part;
+        void *args[] = {&a};
+        e = cudaLaunchKernel(fp, dim3(gp), dim3(kMThreads), args, 0, stream);
+    }
+    if (e != cudaSuccess) return e;
+    // MS-resolution pass
+    MetricArgs b = a;
+    b.partial = ms_part;
+    void *args2[] = {&b};
+    if (!m.in_f32 && m.a32_ms) {
+        const FastFn fm = fast_fn(true, m.bands);
+        const int64_t items = ((m.W / 2 + kStrip - 1) / kStrip) * ((m.H / 2 + kWin - 1) / kWin);
+        e = fast_grid(fm, items, &gm);
+        if (e != cudaSuccess) return e;
+        e = cudaLaunchKernel(fm.fn, dim3(gm), dim3(kFastWarps * 32), args2, fm.smem, stream);
+    } else {
+        const void *fm = m.in_f32 ? ms_fn_nb<float>(m.bands) : ms_fn_nb<uint8_t>(m.bands);
+        const int64_t items = ((m.W / 2 + kWarpCols - 1) / kWarpCols) * ((m.H / 2 + kWin - 1) / kWin);
+        e = grid_for(fm, items, &gm);
+        if (e != cudaSuccess) return e;
+        e = cudaLaunchKernel(fm, dim3(gm), dim3(kMThreads), args2, 0, stream);
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t nwp = (m.H / kWin) * (m.W / kWin), nwm = (m.H / 2 / kWin) * (m.W / 2 / kWin);
+    metrics_finalize_kernel<<<1, 256, 0, stream>>>(pan_part, ms_part, gp, gm, kMetricStride, m.bands,
+                                                   m.want_q, m.H, m.W, nwp, nwm, out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (m.result && m.result != out)
+        e = cudaMemcpyAsync(m.result, out, 4 * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+    return e;
+}
+
+}  // namespace dwtfuse
