@@ -307,7 +307,8 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
     reps = max(1, args.form_reps)
 
     # -- batched: 96 scenes, sides U[256, 8192], 3-8 bands, Haar/D4, float32 out
-    specs = scenegen.batch_specs(n=96, seed=0)
+    # (--forms-small: 12 scenes up to 2048, for profiling only)
+    specs = scenegen.batch_specs(n=12, seed=0, hi=2048) if args.forms_small else scenegen.batch_specs(n=96, seed=0)
     keep, scenes = [], []
     px_bands = 0.0
     nbytes = 0.0
@@ -337,8 +338,8 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
     del keep, scenes, g
     torch.cuda.empty_cache()
 
-    # -- autograd: batch 8 of PAN 4096^2 float32 with 4 MS bands
-    N, B, S = 8, 4, 4096
+    # -- autograd: batch 8 of PAN 4096^2 float32 with 4 MS bands (--forms-small: 2 x 2048^2)
+    N, B, S = (2, 4, 2048) if args.forms_small else (8, 4, 4096)
     pans, mss = [], []
     for i in range(N):
         p, m = scenegen.make_scene(S, S, B, seed=i, device=dev)
@@ -520,6 +521,8 @@ def main() -> None:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-reps", type=int, default=10)
+    ap.add_argument("--forms-small", action="store_true",
+                    help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()

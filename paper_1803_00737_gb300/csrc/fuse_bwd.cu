@@ -10,11 +10,12 @@
 // Haar: grad_M_b = 2x2 block sum of G_b; grad_P = G - repeat2x2(blockmean(G)).
 // D4:   grad_M_b = 2 LL(G_b); grad_P = G - U(LL(G)) with the D4 U of the forward.
 //
-// Same warp-strip decomposition as the forward.  Bands are a run-time loop:
-// the per-band state of a row is consumed before the next band is loaded, so
-// any band count runs in one launch.  D4 reads the four PAN-resolution rows
-// of each band's low-pass window directly (rows 2m+2, 2m+3 are read again by
-// row m+1 from L1/L2, never again from HBM in steady state).
+// Same warp-strip decomposition as the forward: a lane owns PAN columns
+// x..x+3 and walks down R MS rows.  Every band's two new PAN rows are loaded
+// together (all loads of a step in flight at once), and D4 keeps, per band, the
+// row low-pass of the two previous rows (a sliding vertical window), plus the
+// same for G, in registers.  Up to 4 bands per launch; further launches over
+// the remaining bands add their G - U(LL(G)) into grad_P.
 #include "fuse_tile.cuh"
 #include "launch.h"
 
@@ -22,6 +23,7 @@ namespace dwtfuse {
 
 constexpr int kBwdThreads = 256;
 constexpr int kBwdWarps = kBwdThreads / 32;
+constexpr int kBwdChunk = 4;  // bands per launch: every band's rows of a step stay in registers
 
 struct BwdArgs {
     const float *g;               // [bands][H][W]
@@ -43,125 +45,209 @@ __device__ __forceinline__ void store_gms(float *row, const LaneCols &c, bool pa
     }
 }
 
-__device__ __forceinline__ void store_gpan(float *p, bool a4, bool two, const float *v) {
+// grad_P pixels (y, x..x+3): written, or added to what an earlier chunk wrote.
+__device__ __forceinline__ void store_gpan(float *p, bool a4, bool two, bool acc, const float *v) {
+    float w[4] = {v[0], v[1], v[2], v[3]};
+    if (acc) {
+        if (a4) {
+            const float4 o = *reinterpret_cast<const float4 *>(p);
+            w[0] += o.x; w[1] += o.y; w[2] += o.z; w[3] += o.w;
+        } else {
+            const float2 o = *reinterpret_cast<const float2 *>(p);
+            w[0] += o.x; w[1] += o.y;
+            if (two) {
+                const float2 u = *reinterpret_cast<const float2 *>(p + 2);
+                w[2] += u.x; w[3] += u.y;
+            }
+        }
+    }
     if (a4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(p) = make_float4(w[0], w[1], w[2], w[3]);
     } else {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-        if (two) *reinterpret_cast<float2 *>(p + 2) = make_float2(v[2], v[3]);
+        *reinterpret_cast<float2 *>(p) = make_float2(w[0], w[1]);
+        if (two) *reinterpret_cast<float2 *>(p + 2) = make_float2(w[2], w[3]);
     }
 }
 
+template <int NB>
 __device__ __forceinline__ void haar_bwd_item(const BwdArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
-                                              int lane) {
+                                              int b0, bool acc, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0, pair = s.ms2 != 0;
     for (int64_t m = m_s; m < m_e; ++m) {
-        float g0[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int b = 0; b < s.bands; ++b) {
-            const float *gb = s.g + (int64_t)b * HW;
-            float p0[4], p1[4];
-            load_row4(gb + (2 * m) * W, c, a4, p0);
-            load_row4(gb + (2 * m + 1) * W, c, a4, p1);
-            if (c.active) {
-                const float sA = (p0[0] + p0[1]) + (p1[0] + p1[1]);
-                const float sB = (p0[2] + p0[3]) + (p1[2] + p1[3]);
-                store_gms(s.gms[b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
-            }
+        float p0[NB][4], p1[NB][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                g0[q] += p0[q];
-                g1[q] += p1[q];
-            }
+        for (int b = 0; b < NB; ++b) {
+            const float *gb = s.g + (int64_t)(b0 + b) * HW;
+            load_row4(gb + (2 * m) * W, c, a4, p0[b]);
+            load_row4(gb + (2 * m + 1) * W, c, a4, p1[b]);
         }
         if (!c.active) continue;
+        float g0[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const float sA = (p0[b][0] + p0[b][1]) + (p1[b][0] + p1[b][1]);
+            const float sB = (p0[b][2] + p0[b][3]) + (p1[b][2] + p1[b][3]);
+            store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                g0[q] += p0[b][q];
+                g1[q] += p1[b][q];
+            }
+        }
         const float mA = ((g0[0] + g0[1]) + (g1[0] + g1[1])) * 0.25f;
         const float mB = ((g0[2] + g0[3]) + (g1[2] + g1[3])) * 0.25f;
         const float v0[4] = {g0[0] - mA, g0[1] - mA, g0[2] - mB, g0[3] - mB};
         const float v1[4] = {g1[0] - mA, g1[1] - mA, g1[2] - mB, g1[3] - mB};
-        store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, v0);
-        store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, v1);
+        store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, acc, v0);
+        store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, acc, v1);
     }
 }
 
-// D4 low-pass LL(X)(m, n-1..n+1) of one band, and that band's own pixels of
-// rows 2m and 2m+1 (columns x..x+3).
-__device__ __forceinline__ void d4_ll_window(const float *gb, int64_t m, int64_t H, int64_t W,
-                                             const LaneCols &c, bool a4, float *ll, float *own0,
-                                             float *own1) {
-    constexpr float kh[4] = {kH0, kH1, kH2, kH3};
-    ll[0] = ll[1] = ll[2] = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        float v[8], r[3];
-        load_row8(gb + wrap(2 * m + a, H) * W, c, a4, v);
-        d4_rowpass(v, r);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) ll[k] = fmaf(kh[a], r[k], ll[k]);
-        if (a == 0) { own0[0] = v[2]; own0[1] = v[3]; own0[2] = v[4]; own0[3] = v[5]; }
-        if (a == 1) { own1[0] = v[2]; own1[1] = v[3]; own1[2] = v[4]; own1[3] = v[5]; }
-    }
+// Row low-pass at MS columns n and n+1 from the 8 pixels x-2..x+5 (v[2..7]).
+__device__ __forceinline__ void d4_rowpass2(const float *v, float *r) {
+    r[0] = fmaf(kH3, v[5], fmaf(kH2, v[4], fmaf(kH1, v[3], kH0 * v[2])));
+    r[1] = fmaf(kH3, v[7], fmaf(kH2, v[6], fmaf(kH1, v[5], kH0 * v[4])));
 }
 
+template <int NB>
 __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
-                                            int lane) {
+                                            int b0, bool acc, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0, pair = s.ms2 != 0;
-    // Row synthesis of LL(G) for MS row m-1 (vertical pipeline of U).
-    float hprev[4];
+    const float *g = s.g + (int64_t)b0 * HW;
+
+    // Prologue: PAN rows 2mp .. 2mp+3 of every band, mp = m_s - 1 (periodic).
+    const int64_t mp = wrap(m_s - 1, H2);
+    float rb[NB][2][2];      // per band: row low-pass of rows 2m, 2m+1 at MS columns n, n+1
+    float rg0[3], rg1[3];    // G: row low-pass of rows 2m, 2m+1 at n-1, n, n+1
+    float go0[4], go1[4];    // G pixels of rows 2m, 2m+1 (this lane's 4 columns)
+    float hprev[4];          // row synthesis of LL(G)(m-1)
     {
-        const int64_t mp = wrap(m_s - 1, H2);
-        float llg[3] = {0.f, 0.f, 0.f};
-        for (int b = 0; b < s.bands; ++b) {
-            float ll[3], o0[4], o1[4];
-            d4_ll_window(s.g + (int64_t)b * HW, mp, H, W, c, a4, ll, o0, o1);
+        // rows 2mp, 2mp+1: only their band sum G is needed
+        float r0[3], r1[3];
+        {
+            float ga[2][8];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) llg[k] += ll[k];
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) ga[r][k] = 0.f;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    float v[8];
+                    load_row8(g + (int64_t)b * HW + wrap(2 * mp + r, H) * W, c, a4, v);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) ga[r][k] += v[k];
+                }
+            }
+            d4_rowpass(ga[0], r0);
+            d4_rowpass(ga[1], r1);
         }
+        // rows 2mp+2, 2mp+3 (= 2m_s, 2m_s+1): per band low-pass state and G
+        float ga[2][8];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ga[r][k] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float v[8];
+                load_row8(g + (int64_t)b * HW + wrap(2 * mp + 2 + r, H) * W, c, a4, v);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) ga[r][k] += v[k];
+                d4_rowpass2(v, rb[b][r]);
+            }
+        }
+        d4_rowpass(ga[0], rg0);
+        d4_rowpass(ga[1], rg1);
+        float llg[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) llg[k] = fmaf(kH3, rg1[k], fmaf(kH2, rg0[k], fmaf(kH1, r1[k], kH0 * r0[k])));
         hprev[0] = fmaf(kH2, llg[0], kH0 * llg[1]);
         hprev[1] = fmaf(kH3, llg[0], kH1 * llg[1]);
         hprev[2] = fmaf(kH2, llg[1], kH0 * llg[2]);
         hprev[3] = fmaf(kH3, llg[1], kH1 * llg[2]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            go0[q] = ga[0][q + 2];
+            go1[q] = ga[1][q + 2];
+        }
     }
+
     for (int64_t m = m_s; m < m_e; ++m) {
-        float llg[3] = {0.f, 0.f, 0.f};
-        float g0[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int b = 0; b < s.bands; ++b) {
-            float ll[3], o0[4], o1[4];
-            d4_ll_window(s.g + (int64_t)b * HW, m, H, W, c, a4, ll, o0, o1);
-            if (c.active) store_gms(s.gms[b] + m * W2, c, pair, s.kappa * ll[1], s.kappa * ll[2]);
+        // Every band's PAN rows 2m+2 and 2m+3 in flight together.
+        float v[NB][2][8];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) llg[k] += ll[k];
+        for (int b = 0; b < NB; ++b) {
+            const float *gb = g + (int64_t)b * HW;
+            load_row8(gb + wrap(2 * m + 2, H) * W, c, a4, v[b][0]);
+            load_row8(gb + wrap(2 * m + 3, H) * W, c, a4, v[b][1]);
+        }
+        float ga[2][8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                g0[q] += o0[q];
-                g1[q] += o1[q];
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ga[r][k] = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            float n0[2], n1[2];
+            d4_rowpass2(v[b][0], n0);
+            d4_rowpass2(v[b][1], n1);
+            // LL(G_b)(m, n), (m, n+1): column low-pass over rows 2m .. 2m+3
+            const float llA = fmaf(kH3, n1[0], fmaf(kH2, n0[0], fmaf(kH1, rb[b][1][0], kH0 * rb[b][0][0])));
+            const float llB = fmaf(kH3, n1[1], fmaf(kH2, n0[1], fmaf(kH1, rb[b][1][1], kH0 * rb[b][0][1])));
+            if (c.active) store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * llA, s.kappa * llB);
+            rb[b][0][0] = n0[0]; rb[b][0][1] = n0[1];
+            rb[b][1][0] = n1[0]; rb[b][1][1] = n1[1];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                ga[0][k] += v[b][0][k];
+                ga[1][k] += v[b][1][k];
             }
         }
+        float rn0[3], rn1[3], llg[3];
+        d4_rowpass(ga[0], rn0);
+        d4_rowpass(ga[1], rn1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) llg[k] = fmaf(kH3, rn1[k], fmaf(kH2, rn0[k], fmaf(kH1, rg1[k], kH0 * rg0[k])));
         float hc[4];
         hc[0] = fmaf(kH2, llg[0], kH0 * llg[1]);
         hc[1] = fmaf(kH3, llg[0], kH1 * llg[1]);
         hc[2] = fmaf(kH2, llg[1], kH0 * llg[2]);
         hc[3] = fmaf(kH3, llg[1], kH1 * llg[2]);
-        float v0[4], v1[4];
+        float o0[4], o1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            v0[q] = g0[q] - fmaf(kH2, hprev[q], kH0 * hc[q]);
-            v1[q] = g1[q] - fmaf(kH3, hprev[q], kH1 * hc[q]);
+            o0[q] = go0[q] - fmaf(kH2, hprev[q], kH0 * hc[q]);
+            o1[q] = go1[q] - fmaf(kH3, hprev[q], kH1 * hc[q]);
             hprev[q] = hc[q];
         }
         if (c.active) {
-            store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, v0);
-            store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, v1);
+            store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, acc, o0);
+            store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, acc, o1);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            rg0[k] = rn0[k];
+            rg1[k] = rn1[k];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            go0[q] = ga[0][q + 2];
+            go1[q] = ga[1][q + 2];
         }
     }
 }
 
-template <int WAV>
-__global__ void __launch_bounds__(kBwdThreads)
-fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int64_t strips_x, int64_t items, int R) {
+template <int WAV, int NB>
+__global__ void __launch_bounds__(kBwdThreads, 2)
+fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t strips_x, int64_t items, int R) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kBwdWarps;
     for (int64_t it = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5); it < items; it += nwarps) {
@@ -169,11 +255,28 @@ fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int64_t strips_x, int64_t ite
         const int64_t m_s = sy * R;
         const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
         if (WAV == 0)
-            haar_bwd_item(s, sx * kWarpCols, m_s, m_e, lane);
+            haar_bwd_item<NB>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
         else
-            d4_bwd_item(s, sx * kWarpCols, m_s, m_e, lane);
+            d4_bwd_item<NB>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
     }
 }
+
+namespace {
+
+template <int WAV, int NB>
+const void *bwd_fn() { return reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB>); }
+
+template <int WAV>
+const void *bwd_fn_nb(int nb) {
+    switch (nb) {
+        case 1: return bwd_fn<WAV, 1>();
+        case 2: return bwd_fn<WAV, 2>();
+        case 3: return bwd_fn<WAV, 3>();
+        default: return bwd_fn<WAV, 4>();
+    }
+}
+
+}  // namespace
 
 cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
                                  float *gpan, float *const *gms, int R, cudaStream_t stream) {
@@ -193,20 +296,26 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
            (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.ms2 = ms2;
     const ItemGrid ig = item_grid(H, W, R);
-    const void *fn = wavelet == 0 ? reinterpret_cast<const void *>(&fuse_bwd_kernel<0>)
-                                  : reinterpret_cast<const void *>(&fuse_bwd_kernel<1>);
-    int occ = 0, sms = 0;
-    cudaError_t e = resident_blocks(fn, kBwdThreads, &occ);
+    int sms = 0;
+    cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    e = sm_count(&sms);
-    if (e != cudaSuccess) return e;
-    const int64_t need = (ig.items + kBwdWarps - 1) / kBwdWarps;
-    const int64_t cap = (int64_t)sms * occ;
-    const unsigned grid = (unsigned)(need < cap ? need : cap);
-    if (grid == 0) return cudaSuccess;
-    int64_t strips_x = ig.strips_x, items = ig.items;
-    void *args[] = {&s, &strips_x, &items, &R};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, stream);
+    for (int b0 = 0; b0 < bands; b0 += kBwdChunk) {
+        const int nb = bands - b0 < kBwdChunk ? bands - b0 : kBwdChunk;
+        const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb) : bwd_fn_nb<1>(nb);
+        int occ = 0;
+        e = resident_blocks(fn, kBwdThreads, &occ);
+        if (e != cudaSuccess) return e;
+        const int64_t need = (ig.items + kBwdWarps - 1) / kBwdWarps;
+        const int64_t cap = (int64_t)sms * occ;
+        const unsigned grid = (unsigned)(need < cap ? need : cap);
+        if (grid == 0) return cudaSuccess;
+        int acc = b0 > 0;
+        int64_t strips_x = ig.strips_x, items = ig.items;
+        void *args[] = {&s, &b0, &acc, &strips_x, &items, &R};
+        e = cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace dwtfuse

@@ -43,15 +43,25 @@ fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *qu
         }
         const int64_t local = (int64_t)(it - (unsigned long long)t.item_start[lo]);
         const int64_t sx = t.strips_x[lo];
-        // Bands in chunks of kBatchChunk: the PAN low-pass of a chunk's rows is
-        // recomputed (from L1/L2) instead of holding state for 8 bands.
-        for (int b0 = 0; b0 < s.bands; b0 += kBatchChunk) {
-            const int nb = min(kBatchChunk, s.bands - b0);
-            if (s.in_f32)
-                run_item<float, -1, kBatchChunk>(s, local, sx, t.R, b0, nb, lane);
-            else
-                run_item<uint8_t, -1, kBatchChunk>(s, local, sx, t.R, b0, nb, lane);
+        // Exact band count: the same specialised item code as the single-scene
+        // kernel (one of 32 bodies: wavelet x input type x 1..8 bands).
+        const int nb = s.bands;
+#define DWTFUSE_CASE(NBV)                                                                    \
+    case NBV:                                                                                \
+        if (s.in_f32) {                                                                      \
+            if (s.wavelet) run_item<float, 1, NBV>(s, local, sx, t.R, 0, NBV, lane);         \
+            else run_item<float, 0, NBV>(s, local, sx, t.R, 0, NBV, lane);                   \
+        } else {                                                                             \
+            if (s.wavelet) run_item<uint8_t, 1, NBV>(s, local, sx, t.R, 0, NBV, lane);       \
+            else run_item<uint8_t, 0, NBV>(s, local, sx, t.R, 0, NBV, lane);                 \
+        }                                                                                    \
+        break;
+        switch (nb) {
+            DWTFUSE_CASE(1) DWTFUSE_CASE(2) DWTFUSE_CASE(3) DWTFUSE_CASE(4)
+            DWTFUSE_CASE(5) DWTFUSE_CASE(6) DWTFUSE_CASE(7) DWTFUSE_CASE(8)
+            default: break;
         }
+#undef DWTFUSE_CASE
     }
 }
 

@@ -10,7 +10,6 @@ namespace dwtfuse {
 
 constexpr int kChunkBands = 8;     // bands per single-scene launch (more = several launches)
 constexpr int kBatchMaxBands = 8;  // bands per scene in the batched kernel
-constexpr int kBatchChunk = 4;     // bands processed together by one batched work item pass
 constexpr int kMaxScenes = 128;    // scenes per batched launch
 constexpr int kDefaultRows = 32;   // MS rows per warp work item
 constexpr size_t kQueueBytes = 16; // queue counter (8) + status word (4) + pad
