@@ -9,7 +9,8 @@ generated on the device from a seed (scenegen).
 
   value     fused Gpx/s = PAN pixels x bands per second, inputs resident in HBM
   e2e       the same metric with the inputs copied host -> device from pinned
-            memory and the uint8 fused bands copied back every step
+            memory and the uint8 fused bands and quality figures copied back
+            every step (copies and compute of neighbouring steps overlap)
   roofline  fused-forward kernel: algorithmic bytes per launch / mean launch
             time (CUDA events on the launch stream) against the measured HBM
             copy bandwidth
@@ -247,39 +248,69 @@ def run_reference(args) -> None:
 
 # ------------------------------------------------------------------ GPU arm
 
-def measure_e2e(args, pan, ms, out_u, res, step, stream, world, dev) -> dict:
-    """Same step with pinned host inputs copied in and the uint8 fused bands and
-    the four quality figures copied out inside the timed region."""
+def measure_e2e(args, pan, ms, out_f, mws, stream, world, dev) -> dict:
+    """End to end through the public API: every step copies its inputs from
+    pinned host memory to the device, fuses, computes ERGAS/QNR, and copies the
+    uint8 fused bands and the four quality figures back to pinned host memory.
+    Steps are pipelined over three streams (host->device, compute,
+    device->host) with two buffer sets, so one step's copies overlap its
+    neighbours' compute; the timed region spans the first upload to the last
+    download."""
     import torch
-    pan_h = pan.cpu().pin_memory()
-    ms_h = ms.cpu().pin_memory()
-    out_h = torch.empty((BANDS, H, W), dtype=torch.uint8).pin_memory()
-    res_h = torch.empty(4, dtype=torch.float64).pin_memory()
+
+    from paper_1803_00737_gb300 import _C
     Ke = max(1, min(args.steps, args.e2e_steps))
-    for _ in range(2):
-        pan.copy_(pan_h, non_blocking=True)
-        ms.copy_(ms_h, non_blocking=True)
-        step()
-        out_h.copy_(out_u, non_blocking=True)
-        res_h.copy_(res, non_blocking=True)
+    pan_h = [pan.cpu().pin_memory() for _ in range(2)]
+    ms_h = [ms.cpu().pin_memory() for _ in range(2)]
+    out_h = [torch.empty((BANDS, H, W), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    res_h = [torch.empty(4, dtype=torch.float64).pin_memory() for _ in range(2)]
+    pan_d = [pan, torch.empty_like(pan)]
+    ms_d = [ms, torch.empty_like(ms)]
+    out_u = [torch.empty((BANDS, H, W), dtype=torch.uint8, device=dev) for _ in range(2)]
+    res_d = [torch.zeros(4, dtype=torch.float64, device=dev) for _ in range(2)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=False)  # noqa: E731
+    uploaded = [ev() for _ in range(2)]
+    computed = [ev() for _ in range(2)]
+    downloaded = [ev() for _ in range(2)]
+    for e in downloaded + computed:
+        e.record(stream)
+
+    def one(k):
+        i = k % 2
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(computed[i])          # compute k-2 is done with this input set
+            pan_d[i].copy_(pan_h[i], non_blocking=True)
+            ms_d[i].copy_(ms_h[i], non_blocking=True)
+            uploaded[i].record(s_in)
+        with torch.cuda.stream(s_cmp):
+            s_cmp.wait_event(uploaded[i])
+            s_cmp.wait_event(downloaded[i])       # download k-2 is done with this output set
+            _C.dwtfuse_fuse(pan_d[i], ms_d[i], WAVELET, out_f, out_u[i], stream=s_cmp)
+            _C.dwtfuse_metrics(out_u[i], ms_d[i], pan_d[i], mws, res_d[i], stream=s_cmp)
+            computed[i].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(computed[i])
+            out_h[i].copy_(out_u[i], non_blocking=True)
+            res_h[i].copy_(res_d[i], non_blocking=True)
+            downloaded[i].record(s_out)
+
+    for k in range(2):
+        one(k)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(Ke):
-        pan.copy_(pan_h, non_blocking=True)
-        ms.copy_(ms_h, non_blocking=True)
-        step()
-        out_h.copy_(out_u, non_blocking=True)
-        res_h.copy_(res, non_blocking=True)
-    e1.record(stream)
+    e0.record(s_in)
+    for k in range(Ke):
+        one(k)
+    e1.record(s_out)
     torch.cuda.synchronize()
     barrier(world)
     e_el, e_units = aggregate(e0.elapsed_time(e1) / 1e3, float(H * W * BANDS * Ke), world, dev)
     return {"value": e_units / e_el / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": pan.numel() + ms.numel(),
-           "d2h_bytes_per_step": out_u.numel() + res.numel() * 8,
-           "steps": Ke}
+            "h2d_bytes_per_step": pan.numel() + ms.numel(),
+            "d2h_bytes_per_step": out_u[0].numel() + 4 * 8,
+            "steps": Ke, "pipelined": "3 streams, 2 buffer sets"}
 
 
 def _time_ms(fn, reps: int, stream) -> float:
@@ -307,8 +338,8 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
     reps = max(1, args.form_reps)
 
     # -- batched: 96 scenes, sides U[256, 8192], 3-8 bands, Haar/D4, float32 out
-    # (--forms-small: 12 scenes up to 2048, for profiling only)
-    specs = scenegen.batch_specs(n=12, seed=0, hi=2048) if args.forms_small else scenegen.batch_specs(n=96, seed=0)
+    # (--forms-small: 24 scenes up to 4096, for profiling only)
+    specs = scenegen.batch_specs(n=24, seed=0, hi=4096) if args.forms_small else scenegen.batch_specs(n=96, seed=0)
     keep, scenes = [], []
     px_bands = 0.0
     nbytes = 0.0
@@ -320,11 +351,13 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
         px_bands += sp.H * sp.W * sp.bands
         nbytes += sp.H * sp.W * (1.0 + sp.bands * (0.25 + 4.0))
     ws = torch.zeros(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=dev)
-    _C.dwtfuse_fuse_batched(scenes, ws)
+    from paper_1803_00737_gb300 import tune
+    shape = tune.tune_batched(scenes, [(sp.H, sp.W, sp.bands, sp.wavelet) for sp in specs], ws)
+    _C.dwtfuse_fuse_batched(scenes, ws, shape.rows_per_item, shape.blocks_per_sm)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        _C.dwtfuse_fuse_batched(scenes, ws)
+        _C.dwtfuse_fuse_batched(scenes, ws, shape.rows_per_item, shape.blocks_per_sm)
     g.replay()
     ms_b = _time_ms(g.replay, reps, stream)
     out["batched"] = {
@@ -334,12 +367,14 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
         "roofline": {"achieved": nbytes / (ms_b / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": nbytes / (ms_b / 1e3) / 1e9 / peak},
         "gpu_launches_per_replay": 1,
+        "launch_shape": {"rows_per_item": shape.rows_per_item, "blocks_per_sm": shape.blocks_per_sm,
+                         "chosen_by": "autotuner (paper_1803_00737_gb300.tune)"},
     }
     del keep, scenes, g
     torch.cuda.empty_cache()
 
-    # -- autograd: batch 8 of PAN 4096^2 float32 with 4 MS bands (--forms-small: 2 x 2048^2)
-    N, B, S = (2, 4, 2048) if args.forms_small else (8, 4, 4096)
+    # -- autograd: batch 8 of PAN 4096^2 float32 with 4 MS bands (--forms-small: 2 x 4096^2)
+    N, B, S = (2, 4, 4096) if args.forms_small else (8, 4, 4096)
     pans, mss = [], []
     for i in range(N):
         p, m = scenegen.make_scene(S, S, B, seed=i, device=dev)
@@ -459,7 +494,7 @@ def run_ours(args) -> None:
 
     e2e = None
     if not args.no_e2e:
-        e2e = measure_e2e(args, pan, ms, out_u, res, step, stream, world, dev)
+        e2e = measure_e2e(args, pan, ms, out_f, mws, stream, world, dev)
 
     peak, peak_kind = measured_hbm()
     mean_fwd_s = statistics.mean(fwd_ms) / 1e3 / fwd_launches
