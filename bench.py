@@ -50,7 +50,11 @@ FALLBACK_HBM_GBS = 6800.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused forward
 # at this workload, keyed by the hash of the kernel sources it was taken on.
-KNOWN_TRAFFIC: dict[str, float] = {}
+KNOWN_TRAFFIC: dict[str, float] = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
+    # read 694,831,360 + write 7,991,928,320 (profiles/fuse_fwd_d4_4096x4096_b6.md)
+    "c468ee287701": 8686759680.0,
+}
 
 
 def kernel_hash() -> str:
@@ -368,7 +372,10 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
                      "frac": nbytes / (ms_b / 1e3) / 1e9 / peak},
         "gpu_launches_per_replay": 1,
         "launch_shape": {"rows_per_item": shape.rows_per_item, "blocks_per_sm": shape.blocks_per_sm,
-                         "chosen_by": "autotuner (paper_1803_00737_gb300.tune)"},
+                         "chosen_by": "autotuner (paper_1803_00737_gb300.tune)",
+                         "candidates_ms": tune.load_cache()["entries"].get(
+                             tune.current_device_key() + "|" + tune.batched_class(
+                                 [(sp.H, sp.W, sp.bands, sp.wavelet) for sp in specs]), {}).get("times_ms")},
     }
     del keep, scenes, g
     torch.cuda.empty_cache()

@@ -211,8 +211,10 @@ int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, int rows_pe
                                  int blocks_per_sm, void *stream);
 
 /*
- * Launch-shape knob of dwtfuse_fuse for the autotuner: MS rows per warp work
- * item (0 restores the default).  Process-wide; not thread-safe.
+ * Launch-shape knob of dwtfuse_fuse and dwtfuse_fuse_backward for the
+ * autotuner: MS rows per warp work item.  0 (the default) picks, per launch,
+ * the height in [16, 64] that fills the last wave of the persistent grid.
+ * Process-wide.
  */
 int dwtfuse_set_rows_per_item(int rows);
 

@@ -14,7 +14,7 @@ namespace {
 std::mutex g_mu;
 std::unordered_map<const void *, int> g_occ;
 std::unordered_map<int, int> g_sms;
-std::atomic<int> g_rows{kDefaultRows};
+std::atomic<int> g_rows{0};  // 0: balanced_rows() per launch
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 }  // namespace
 
@@ -138,7 +138,7 @@ int dwtfuse_last_cuda_error(void) { return (int)g_last_cuda; }
 
 int dwtfuse_set_rows_per_item(int rows) {
     if (rows < 0 || rows > 4096) return DWTFUSE_EINVAL;
-    g_rows.store(rows == 0 ? kDefaultRows : rows, std::memory_order_relaxed);
+    g_rows.store(rows, std::memory_order_relaxed);
     return DWTFUSE_OK;
 }
 

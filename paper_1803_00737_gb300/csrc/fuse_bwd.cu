@@ -295,7 +295,6 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     s.a4 = (W % 4 == 0) && (reinterpret_cast<uintptr_t>(g) % 16 == 0) &&
            (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.ms2 = ms2;
-    const ItemGrid ig = item_grid(H, W, R);
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
@@ -305,13 +304,15 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
         int occ = 0;
         e = resident_blocks(fn, kBwdThreads, &occ);
         if (e != cudaSuccess) return e;
-        const int64_t need = (ig.items + kBwdWarps - 1) / kBwdWarps;
         const int64_t cap = (int64_t)sms * occ;
+        int Rl = R > 0 ? R : balanced_rows(H, W, cap * kBwdWarps);
+        const ItemGrid ig = item_grid(H, W, Rl);
+        const int64_t need = (ig.items + kBwdWarps - 1) / kBwdWarps;
         const unsigned grid = (unsigned)(need < cap ? need : cap);
         if (grid == 0) return cudaSuccess;
         int acc = b0 > 0;
         int64_t strips_x = ig.strips_x, items = ig.items;
-        void *args[] = {&s, &b0, &acc, &strips_x, &items, &R};
+        void *args[] = {&s, &b0, &acc, &strips_x, &items, &Rl};
         e = cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, stream);
         if (e != cudaSuccess) return e;
     }

@@ -94,7 +94,6 @@ void *fwd_kernel_ptr(bool f32, int wav, int nb) {
 }  // namespace
 
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream) {
-    const ItemGrid g = item_grid(s.H, s.W, R);
     for (int b0 = 0; b0 < s.bands; b0 += kChunkBands) {
         const int nb = s.bands - b0 < kChunkBands ? s.bands - b0 : kChunkBands;
         void *fn = fwd_kernel_ptr(s.in_f32 != 0, s.wavelet, nb);
@@ -105,13 +104,15 @@ cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream
         int sms = 0;
         e = sm_count(&sms);
         if (e != cudaSuccess) return e;
-        const int64_t need = (g.items + kWarps - 1) / kWarps;
         const int64_t cap = (int64_t)sms * occ;
+        int Rl = R > 0 ? R : balanced_rows(s.H, s.W, cap * kWarps);
+        const ItemGrid g = item_grid(s.H, s.W, Rl);
+        const int64_t need = (g.items + kWarps - 1) / kWarps;
         const unsigned grid = (unsigned)(need < cap ? need : cap);
         if (grid == 0) continue;
         SceneArgs sa = s;
         int64_t strips_x = g.strips_x, items = g.items;
-        void *args[] = {&sa, (void *)&b0, &strips_x, &items, &R};
+        void *args[] = {&sa, (void *)&b0, &strips_x, &items, &Rl};
         e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream);
         if (e != cudaSuccess) return e;
     }

@@ -11,7 +11,7 @@ namespace dwtfuse {
 constexpr int kChunkBands = 8;     // bands per single-scene launch (more = several launches)
 constexpr int kBatchMaxBands = 8;  // bands per scene in the batched kernel
 constexpr int kMaxScenes = 128;    // scenes per batched launch
-constexpr int kDefaultRows = 32;   // MS rows per warp work item
+constexpr int kDefaultRows = 32;   // MS rows per warp work item (batched default)
 constexpr size_t kQueueBytes = 16; // queue counter (8) + status word (4) + pad
 
 // Scene table of a batched launch.  It travels by value in the kernel
@@ -48,6 +48,24 @@ struct MetricLaunch {
     double *workspace;  // kMetricWorkspaceBytes, 8-byte aligned
     double *result;     // device pointer for the 4 results, or nullptr
 };
+
+// MS rows per work item that balance the last wave of a grid of `warps`
+// warps: minimises ceil(items / warps) * (R + 1) over R in [16, 64] (the +1
+// is the D4 prologue row of every item); ties go to the taller item.
+inline int balanced_rows(int64_t H, int64_t W, int64_t warps) {
+    int best = kDefaultRows;
+    double best_cost = 1e300;
+    for (int R = 16; R <= 64; ++R) {
+        const ItemGrid g = item_grid(H, W, R);
+        const int64_t waves = (g.items + warps - 1) / warps;
+        const double cost = (double)waves * (double)(R + 1);
+        if (cost <= best_cost) {
+            best_cost = cost;
+            best = R;
+        }
+    }
+    return best;
+}
 
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);

@@ -751,9 +751,11 @@ metrics_ms_kernel(const __grid_constant__ MetricArgs a) {
 
 // --------------------------------------------------------------- finalize
 
-// One CTA: sums the per-CTA partial rows in a fixed order and writes
-// out[0..3] = ERGAS, QNR, D_lambda, D_s (QNR terms NaN when not requested or
-// when no full window exists at either resolution).
+// One CTA: sums the per-CTA partial rows and writes out[0..3] = ERGAS, QNR,
+// D_lambda, D_s (QNR terms NaN when not requested or when no full window
+// exists at either resolution).  Each warp reduces one column of partials:
+// lanes stride over the CTAs, then a xor butterfly (a fixed order, so the
+// result is the same on every run).
 __global__ void __launch_bounds__(256)
 metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, int ctas_ms,
                         int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
@@ -761,12 +763,16 @@ metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_
     __shared__ double tot_pan[64 + kMaxBands];
     __shared__ double tot_ms[64 + kMaxBands];
     const int P = nb * (nb - 1) / 2 + nb;
-    for (int k = threadIdx.x; k < P + nb; k += blockDim.x) {
-        double a = 0.0, b = 0.0;
-        for (int c = 0; c < ctas_pan; ++c) a += pan_part[(int64_t)c * stride + k];
-        for (int c = 0; c < ctas_ms; ++c) b += ms_part[(int64_t)c * stride + k];
-        tot_pan[k] = a;
-        tot_ms[k] = b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = warp; k < 2 * (P + nb); k += nwarps) {
+        const bool ms = k >= P + nb;
+        const int kk = ms ? k - (P + nb) : k;
+        const double *part = ms ? ms_part : pan_part;
+        const int ctas = ms ? ctas_ms : ctas_pan;
+        double a = 0.0;
+        for (int c = lane; c < ctas; c += 32) a += part[(int64_t)c * stride + kk];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) (ms ? tot_ms : tot_pan)[kk] = a;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
