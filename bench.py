@@ -15,9 +15,11 @@ generated on the device from a seed (scenegen).
             time (CUDA events on the launch stream) against the measured HBM
             copy bandwidth
   forms     the other forms of the path, timed after the main region on their
-            own workloads: 96 uneven scenes through one captured batched launch,
-            and forward + backward of a batch of 8 float32 4096^2 scenes (4 bands)
-            next to the plain forward of the same batch
+            own workloads: 96 uneven scenes through one captured batched launch;
+            forward + backward of a batch of 8 float32 4096^2 scenes (4 bands)
+            next to the plain forward of the same batch; and 12 scenes of
+            8192^2 .. 32768^2 x 8 bands through one graph of forward, metrics and
+            backward (outputs streamed through one slot)
 
 Multi-GPU: the path does not shard here (replicas only): each rank fuses its
 own scene, timing is the max over ranks, value sums every rank's pixels.
@@ -428,6 +430,98 @@ def measure_forms(args, dev, peak: float, world: int) -> dict:
     return out
 
 
+def measure_config4(args, dev, peak: float) -> dict:
+    """12 square scenes, sides even U[8192, 32768], 8 MS bands, D4: per scene the
+    batched forward (float32 + uint8), ERGAS/QNR of the uint8 product and the
+    adjoint with grad_out = F (loss 1/2 ||F||^2), all in one captured CUDA graph.
+    Inputs of every scene stay resident (~17 GB); the outputs and gradients
+    stream through one slot sized for the largest scene (~60 GB), so the whole
+    workload (~445 GB if everything were resident) runs in a bounded pool."""
+    import torch
+
+    import scenegen
+    from paper_1803_00737_gb300 import _C
+    specs = scenegen.batch_specs(n=12, seed=0, lo=8192, hi=32768, bands=(8, 8),
+                                 wavelets=(scenegen.D4,), square=True)
+    if args.forms_small:
+        specs = [scenegen.SceneSpec(s.H // 4, s.W // 4, s.bands, s.wavelet, s.seed) for s in specs[:3]]
+    B = 8
+    inputs = [scenegen.make_scene(sp.H, sp.W, B, seed=sp.seed, blob_scale=16.0, device=dev) for sp in specs]
+    torch.cuda.empty_cache()
+    n_max = max(sp.H * sp.W for sp in specs)
+    out_f = torch.empty(B * n_max, dtype=torch.float32, device=dev)
+    out_u = torch.empty(B * n_max, dtype=torch.uint8, device=dev)
+    gp_s = torch.empty(n_max, dtype=torch.float32, device=dev)
+    gm_s = torch.empty(B * n_max // 4, dtype=torch.float32, device=dev)
+    ws = torch.zeros(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=dev)
+    mws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
+    res = torch.zeros((len(specs), 4), dtype=torch.float64, device=dev)
+    views = []
+    for sp, (p, m) in zip(specs, inputs):
+        n = sp.H * sp.W
+        f = out_f[:B * n].view(B, sp.H, sp.W)
+        u = out_u[:B * n].view(B, sp.H, sp.W)
+        views.append((sp, p, m, f, u, gp_s[:n].view(sp.H, sp.W),
+                      gm_s[:B * n // 4].view(B, sp.H // 2, sp.W // 2), _C.make_scene(p, m, sp.wavelet, f, u)))
+
+    def run(ev=None):
+        for k, (sp, p, m, f, u, gp, gm, scene) in enumerate(views):
+            if ev is not None:
+                ev[k][0].record()
+            _C.dwtfuse_fuse_batched([scene], ws)
+            if ev is not None:
+                ev[k][1].record()
+            _C.dwtfuse_metrics(u, m, p, mws, res[k])
+            if ev is not None:
+                ev[k][2].record()
+            _C.dwtfuse_fuse_backward(f, sp.wavelet, gp, gm)
+            if ev is not None:
+                ev[k][3].record()
+
+    run()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in views]
+    run(ev)
+    torch.cuda.synchronize()
+    t_f = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    t_m = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    t_b = sum(e[2].elapsed_time(e[3]) for e in ev) / 1e3
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        run()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        run()
+    g.replay()
+    torch.cuda.synchronize()
+    ms_graph = _time_ms(g.replay, max(1, min(3, args.form_reps)), torch.cuda.current_stream())
+    px = sum(sp.H * sp.W for sp in specs)
+    units = px * B
+    fb = px * (1.0 + B * (0.25 + 4.0 + 1.0))
+    mb = px * (B * 1.0 + 1.0 + B * 0.25) + px * (B * 0.25 + 1.0)
+    bb = px * (4.0 * B + 4.0 + B)
+    rf = lambda nbytes, t: {"achieved": nbytes / t / 1e9, "frac": nbytes / t / 1e9 / peak}  # noqa: E731
+    q = res.cpu().numpy()
+    del views, inputs, out_f, out_u, gp_s, gm_s, g
+    torch.cuda.empty_cache()
+    return {
+        "workload": "12 square scenes, PAN sides even U[8192, 32768] uint8, 8 MS bands, D4: batched "
+                    "forward (float32 + uint8) + ERGAS/QNR of the uint8 product + adjoint with "
+                    "grad_out = F, one CUDA graph, outputs streamed through one slot"
+                    + (" [reduced: --forms-small]" if args.forms_small else ""),
+        "scenes": [sp.H for sp in specs], "pan_gpx": px / 1e9,
+        "fwd_bwd_metrics_gpxs": units / (ms_graph / 1e3) / 1e9, "unit": UNIT, "graph_ms": ms_graph,
+        "per_kernel": {"fused_forward": {"ms": t_f * 1e3, **rf(fb, t_f)},
+                       "metrics": {"ms": t_m * 1e3, **rf(mb, t_m)},
+                       "adjoint": {"ms": t_b * 1e3, **rf(bb, t_b)}},
+        "qnr_range": [float(q[:, 1].min()), float(q[:, 1].max())],
+        "gpu_launches_per_replay": len(specs) * (1 + 3 + 2),
+    }
+
+
 def run_ours(args) -> None:
     import torch
 
@@ -530,6 +624,7 @@ def run_ours(args) -> None:
         del out_f
         torch.cuda.empty_cache()
         forms = measure_forms(args, dev, peak, world)
+        forms["config4"] = measure_config4(args, dev, peak)
 
     if rank == 0:
         print(json.dumps({
