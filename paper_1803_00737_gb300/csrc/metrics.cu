@@ -298,10 +298,11 @@ metrics_pan_kernel(const __grid_constant__ MetricArgs a) {
 
 // --------------------------------------------------------------- 8-bit fast paths
 
-// Asynchronous global -> shared copies (the per-warp row ring below).
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+// Asynchronous global -> shared copy of one 16-byte chunk; bytes past
+// `valid` are zero-filled (the source is not read there).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned valid) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(valid) : "memory");
 }
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -311,29 +312,99 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// 8-bit product and inputs, W % 16 == 0, 16-byte aligned planes (8 for MS).
-// A lane owns 16 consecutive pixels of a row, a window is two lanes, a warp
-// strip is 512 columns (16 windows) x 32 rows.  Each lane streams its rows
-// through a private ring of kStages rows in shared memory with cp.async, so
-// several rows of every band are in flight without holding registers; it
-// reads back only the bytes it copied, so no barrier is needed.  Shifted
-// values are signed bytes (X ^ 0x80 = X - 128) and every sum is a dp4a over 4
-// pixels, exact in int32.
+// Copies the bytes [a0, a0 + span) of one image row into shared memory as
+// 16-byte chunks starting at the aligned address floor16(a0), so the row's
+// byte i lands at dst[(a0 & 15) + i].  Chunks are spread over the lanes.
+// Bytes outside the image plane [lo, hi) are never read: a chunk crossing
+// hi is zero-filled past it; a chunk starting before lo (a plane that is
+// not 16-byte aligned) is copied byte by byte.
+__device__ __forceinline__ void copy_row(unsigned char *dst, const uint8_t *a0, int span,
+                                         const uint8_t *lo, const uint8_t *hi, int lane) {
+    const uintptr_t ua = reinterpret_cast<uintptr_t>(a0);
+    const uint8_t *c0 = reinterpret_cast<const uint8_t *>(ua & ~(uintptr_t)15);
+    const int nchunks = ((int)(ua & 15) + span + 15) >> 4;
+    if (c0 >= lo && c0 + 16 * nchunks <= hi) {
+        // the whole span lies inside the plane (every row but a plane's last)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {  // up to 96 chunks: 1024 staged bytes + slack
+            const int k = lane + 32 * t;
+            if (k < nchunks) cp_async16(dst + 16 * k, c0 + 16 * k, 16u);
+        }
+        return;
+    }
+    for (int k = lane; k < nchunks; k += 32) {
+        const uint8_t *src = c0 + 16 * k;
+        if (src >= hi || src + 16 <= lo) continue;
+        if (src >= lo) {
+            const int64_t v = hi - src;
+            cp_async16(dst + 16 * k, src, v >= 16 ? 16u : (unsigned)v);
+        } else {
+            for (int i = 0; i < 16; ++i)
+                if (src + i >= lo && src + i < hi) dst[16 * k + i] = __ldg(src + i);
+        }
+    }
+}
+
+// NW 32-bit words of a staged row starting at byte offset off (one offset per
+// image row, the same for every lane, so the branches are uniform).
+template <int NW>
+__device__ __forceinline__ void read_words(const unsigned char *base, int off, uint32_t *w) {
+    if (NW % 4 == 0 && (off & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < NW / 4; ++k) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(base + off + 16 * k);
+            w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
+        }
+        return;
+    }
+    if (NW == 2 && (off & 7) == 0) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(base + off);
+        w[0] = q.x;
+        w[1] = q.y;
+        return;
+    }
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(base + (off & ~3));
+    const int sh = (off & 3) * 8;
+    uint32_t r[NW + 1];
+#pragma unroll
+    for (int k = 0; k <= NW; ++k) r[k] = p[k];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = sh ? __funnelshift_r(r[k], r[k + 1], sh) : r[k];
+}
+
+// Byte mask keeping the first `v` bytes of word q of a lane (v may exceed 4q+3).
+__device__ __forceinline__ uint32_t keep_mask(int v, int q) {
+    const int n = v - 4 * q;
+    return n >= 4 ? 0xffffffffu : (n <= 0 ? 0u : (0xffffffffu >> (32 - 8 * n)));
+}
+
+// 8-bit product and inputs, any even width and plane alignment.  A lane owns
+// 16 consecutive pixels of a row, a window is two lanes, a warp strip is 512
+// columns (16 windows) x 32 rows.  Each warp streams its strip's rows through
+// a ring of kStages rows in shared memory with cp.async, so several rows of
+// every band are in flight without holding registers.  Shifted values are
+// signed bytes (X ^ 0x80 = X - 128) and every sum is a dp4a over 4 pixels,
+// exact in int32.
 constexpr int kLanePx = 16;
 constexpr int kStrip = 32 * kLanePx;
 constexpr int kWinPerStrip = kStrip / kWin;
 constexpr int kFastWarps = 8;
+constexpr int kImgRow = kStrip + 32;       // staged bytes per image row (alignment slack, 16-aligned)
+constexpr int kMsRow = kStrip / 2 + 32;    // staged bytes per MS row in the PAN pass
 
 template <int NB>
 struct FastPan {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
     static constexpr int kStages = NB <= 6 ? 4 : 3;
-    static constexpr int kRowBytes = K * 512 + NB * 256;  // per warp: F bands + PAN (16 B/lane), MS (8 B/lane)
+    static constexpr int kRowBytes = K * kImgRow + NB * kMsRow;
     static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
                                  kFastWarps * NB * 8;
 };
 
-template <int NB>
+// GEN = false: rows of every plane start on 16-byte boundaries (W % 16 == 0,
+// aligned planes): one chunk per lane and image, read back by the same lane.
+// GEN = true: any width and alignment, rows shifted into place.
+template <int NB, bool GEN>
 __global__ void __launch_bounds__(kFastWarps * 32, 1)
 metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     using C = FastPan<NB>;
@@ -347,32 +418,50 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     double se_tot[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) se_tot[b] = 0.0;
-    const int64_t H = a.H, W = a.W, W2 = W >> 1, HW = H * W;
+    const int64_t H = a.H, W = a.W, W2 = W >> 1, H2 = H >> 1, HW = H * W;
     const uint8_t *F = static_cast<const uint8_t *>(a.fused);
     const uint8_t *pan = static_cast<const uint8_t *>(a.pan);
     const int64_t sx_n = (W + kStrip - 1) / kStrip, sy_n = (H + kWin - 1) / kWin;
     const int64_t items = sx_n * sy_n;
     const int64_t nw = (int64_t)gridDim.x * kFastWarps;
     for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
-        const int64_t x = (it % sx_n) * kStrip + kLanePx * lane;
+        const int64_t x0 = (it % sx_n) * kStrip;
+        const int64_t x = x0 + kLanePx * lane;
         const int64_t y0 = (it / sx_n) * kWin;
         const bool act = x < W;
+        const int nval = act ? (int)min((int64_t)kLanePx, W - x) : 0;  // valid pixels of this lane
         const int64_t xwin = x - kLanePx * (lane & 1);
         const bool full = a.want_q && (y0 + kWin <= H) && (xwin + kWin <= W);
         const int nrows = (int)min((int64_t)kWin, H - y0);
-        // Row r of this strip into ring slot r % S (only this lane's bytes).
+        const int span = (int)min((int64_t)kStrip, W - x0);
+        // Row r of this strip into ring slot r % S.
         auto issue = [&](int r) {
-            if (r < nrows && act) {
+            if (r < nrows) {
                 unsigned char *slot = ring + (r % S) * RB;
                 const int64_t y = y0 + r;
+                if (GEN) {
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    cp_async16(slot + b * 512 + lane * 16, F + (int64_t)b * HW + y * W + x);
-                if (a.want_q) cp_async16(slot + NB * 512 + lane * 16, pan + y * W + x);
+                    for (int b = 0; b < NB; ++b) {
+                        const uint8_t *plane = F + (int64_t)b * HW;
+                        copy_row(slot + b * kImgRow, plane + y * W + x0, span, plane, plane + HW, lane);
+                    }
+                    if (a.want_q) copy_row(slot + NB * kImgRow, pan + y * W + x0, span, pan, pan + HW, lane);
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    cp_async8(slot + K * 512 + b * 256 + lane * 8,
-                              static_cast<const uint8_t *>(a.ms[b]) + (y >> 1) * W2 + (x >> 1));
+                    for (int b = 0; b < NB; ++b) {
+                        const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
+                        copy_row(slot + K * kImgRow + b * kMsRow, m + (y >> 1) * W2 + (x0 >> 1), span / 2, m,
+                                 m + H2 * W2, lane);
+                    }
+                } else if (act) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        cp_async16(slot + b * kImgRow + lane * 16, F + (int64_t)b * HW + y * W + x, 16u);
+                    if (a.want_q) cp_async16(slot + NB * kImgRow + lane * 16, pan + y * W + x, 16u);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        cp_async8(slot + K * kImgRow + b * kMsRow + lane * 8,
+                                  static_cast<const uint8_t *>(a.ms[b]) + (y >> 1) * W2 + (x >> 1));
+                }
             }
             cp_async_commit();
         };
@@ -386,38 +475,55 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) se[b] = 0;
         for (int r = 0; r < nrows; ++r) {
+            if (GEN) __syncwarp();  // every lane is done with the slot refilled next
             issue(r + S - 1);
             cp_async_wait<S - 1>();
+            if (GEN) __syncwarp();  // every lane's copies of row r are in place
             if (!act) continue;
             const unsigned char *slot = ring + (r % S) * RB;
-            uint4 f[NB];
-            uint2 m[NB];
+            const int64_t y = y0 + r;
+            uint32_t f[NB][4], m[NB][2];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                f[b] = *reinterpret_cast<const uint4 *>(slot + b * 512 + lane * 16);
-                m[b] = *reinterpret_cast<const uint2 *>(slot + K * 512 + b * 256 + lane * 8);
+                if (GEN) {
+                    const int offf = (int)(reinterpret_cast<uintptr_t>(F + (int64_t)b * HW + y * W + x0) & 15) + kLanePx * lane;
+                    read_words<4>(slot + b * kImgRow, offf, f[b]);
+                    const uint8_t *mrow = static_cast<const uint8_t *>(a.ms[b]) + (y >> 1) * W2 + (x0 >> 1);
+                    const int offm = (int)(reinterpret_cast<uintptr_t>(mrow) & 15) + (kLanePx / 2) * lane;
+                    read_words<2>(slot + K * kImgRow + b * kMsRow, offm, m[b]);
+                } else {
+                    const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + b * kImgRow + lane * 16);
+                    f[b][0] = q4.x; f[b][1] = q4.y; f[b][2] = q4.z; f[b][3] = q4.w;
+                    const uint2 q2 = *reinterpret_cast<const uint2 *>(slot + K * kImgRow + b * kMsRow + lane * 8);
+                    m[b][0] = q2.x; m[b][1] = q2.y;
+                }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                const uint32_t keep = GEN ? keep_mask(nval, q) : 0xffffffffu;
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
-                    const uint32_t fw = q == 0 ? f[b].x : q == 1 ? f[b].y : q == 2 ? f[b].z : f[b].w;
-                    const uint32_t mw = q < 2 ? m[b].x : m[b].y;
                     // MS pixels 2q, 2q+1 of this lane, each repeated twice
-                    const uint32_t rep = __byte_perm(mw, 0u, (q & 1) ? 0x3322u : 0x1100u);
-                    const uint32_t d = __vabsdiffu4(fw, rep);
+                    const uint32_t rep = __byte_perm(m[b][q >> 1], 0u, (q & 1) ? 0x3322u : 0x1100u);
+                    const uint32_t d = __vabsdiffu4(f[b][q], rep) & keep;
                     se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
                 }
             }
             if (full) {
-                const uint4 pw = *reinterpret_cast<const uint4 *>(slot + NB * 512 + lane * 16);
+                uint32_t pw[4];
+                if (GEN) {
+                    const int offp = (int)(reinterpret_cast<uintptr_t>(pan + y * W + x0) & 15) + kLanePx * lane;
+                    read_words<4>(slot + NB * kImgRow, offp, pw);
+                } else {
+                    const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + NB * kImgRow + lane * 16);
+                    pw[0] = q4.x; pw[1] = q4.y; pw[2] = q4.z; pw[3] = q4.w;
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     int v[K];
 #pragma unroll
-                    for (int b = 0; b < NB; ++b)
-                        v[b] = (int)((q == 0 ? f[b].x : q == 1 ? f[b].y : q == 2 ? f[b].z : f[b].w) ^ 0x80808080u);
-                    v[NB] = (int)((q == 0 ? pw.x : q == 1 ? pw.y : q == 2 ? pw.z : pw.w) ^ 0x80808080u);
+                    for (int b = 0; b < NB; ++b) v[b] = (int)(f[b][q] ^ 0x80808080u);
+                    v[NB] = (int)(pw[q] ^ 0x80808080u);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         s1[k] = __dp4a(v[k], 0x01010101, s1[k]);
@@ -489,7 +595,8 @@ template <int NB>
 struct FastMs {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
     static constexpr int kStages = NB <= 6 ? 4 : 3;
-    static constexpr int kRowBytes = NB * 512 + 4 * 512;  // per warp: MS bands (16 B/lane), 2 PAN rows (32 B/lane each)
+    static constexpr int kPanRow = 2 * kStrip + 32;  // 32 PAN pixels per lane
+    static constexpr int kRowBytes = NB * kImgRow + 2 * kPanRow;
     static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
                                  kFastWarps * NB * 8;
 };
@@ -498,11 +605,12 @@ struct FastMs {
 // 2 x 32 PAN pixels above them).  MS values are signed bytes (dp4a); PAN~ is
 // carried as Z = 4 PAN~ - 512 (the 2x2 sum, exact) and its products use
 // integer multiply-adds.
-template <int NB>
+// GEN as for the PAN pass (aligned: W % 32 == 0, 16-byte aligned MS and PAN).
+template <int NB, bool GEN>
 __global__ void __launch_bounds__(kFastWarps * 32, 1)
 metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
     using C = FastMs<NB>;
-    constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
+    constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes, PR = C::kPanRow;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *ring = smem + warp * S * RB;
@@ -512,31 +620,48 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
     double sum_tot[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) sum_tot[b] = 0.0;
-    const int64_t H2 = a.H >> 1, W2 = a.W >> 1, W = a.W;
+    const int64_t H2 = a.H >> 1, W2 = a.W >> 1, W = a.W, HW = a.H * a.W;
     const uint8_t *pan = static_cast<const uint8_t *>(a.pan);
     const int64_t sx_n = (W2 + kStrip - 1) / kStrip, sy_n = (H2 + kWin - 1) / kWin;
     const int64_t items = sx_n * sy_n;
     const int64_t nw = (int64_t)gridDim.x * kFastWarps;
     for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
-        const int64_t j = (it % sx_n) * kStrip + kLanePx * lane;  // MS column
+        const int64_t j0 = (it % sx_n) * kStrip;
+        const int64_t j = j0 + kLanePx * lane;  // MS column
         const int64_t i0 = (it / sx_n) * kWin;
         const bool act = j < W2;
+        const int nval = act ? (int)min((int64_t)kLanePx, W2 - j) : 0;
         const int64_t jwin = j - kLanePx * (lane & 1);
         const bool full = a.want_q && (i0 + kWin <= H2) && (jwin + kWin <= W2);
+        const bool any_full = __any_sync(0xffffffffu, full);
         const int nrows = (int)min((int64_t)kWin, H2 - i0);
+        const int span = (int)min((int64_t)kStrip, W2 - j0);
         auto issue = [&](int r) {
-            if (r < nrows && act) {
+            if (r < nrows) {
                 unsigned char *slot = ring + (r % S) * RB;
                 const int64_t i = i0 + r;
+                if (GEN) {
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    cp_async16(slot + b * 512 + lane * 16, static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j);
-                if (full) {
-                    const uint8_t *p0 = pan + (2 * i) * W + 2 * j;
-                    cp_async16(slot + NB * 512 + lane * 32, p0);
-                    cp_async16(slot + NB * 512 + lane * 32 + 16, p0 + 16);
-                    cp_async16(slot + NB * 512 + 1024 + lane * 32, p0 + W);
-                    cp_async16(slot + NB * 512 + 1024 + lane * 32 + 16, p0 + W + 16);
+                    for (int b = 0; b < NB; ++b) {
+                        const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
+                        copy_row(slot + b * kImgRow, m + i * W2 + j0, span, m, m + H2 * W2, lane);
+                    }
+                    if (any_full) {
+                        copy_row(slot + NB * kImgRow, pan + (2 * i) * W + 2 * j0, 2 * span, pan, pan + HW, lane);
+                        copy_row(slot + NB * kImgRow + PR, pan + (2 * i + 1) * W + 2 * j0, 2 * span, pan, pan + HW,
+                                 lane);
+                    }
+                } else if (act) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        cp_async16(slot + b * kImgRow + lane * 16, static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j, 16u);
+                    if (full) {
+                        const uint8_t *p0 = pan + (2 * i) * W + 2 * j;
+                        cp_async16(slot + NB * kImgRow + lane * 32, p0, 16u);
+                        cp_async16(slot + NB * kImgRow + lane * 32 + 16, p0 + 16, 16u);
+                        cp_async16(slot + NB * kImgRow + PR + lane * 32, p0 + W, 16u);
+                        cp_async16(slot + NB * kImgRow + PR + lane * 32 + 16, p0 + W + 16, 16u);
+                    }
                 }
             }
             cp_async_commit();
@@ -551,30 +676,47 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) sm[b] = 0;
         for (int r = 0; r < nrows; ++r) {
+            if (GEN) __syncwarp();
             issue(r + S - 1);
             cp_async_wait<S - 1>();
+            if (GEN) __syncwarp();
             if (!act) continue;
             const unsigned char *slot = ring + (r % S) * RB;
-            uint4 mv[NB];
+            const int64_t i = i0 + r;
+            uint32_t mv[NB][4];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                mv[b] = *reinterpret_cast<const uint4 *>(slot + b * 512 + lane * 16);
-                sm[b] = (int)__dp4a(mv[b].x, 0x01010101u, (unsigned)sm[b]);
-                sm[b] = (int)__dp4a(mv[b].y, 0x01010101u, (unsigned)sm[b]);
-                sm[b] = (int)__dp4a(mv[b].z, 0x01010101u, (unsigned)sm[b]);
-                sm[b] = (int)__dp4a(mv[b].w, 0x01010101u, (unsigned)sm[b]);
+                if (GEN) {
+                    const uint8_t *mrow = static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j0;
+                    read_words<4>(slot + b * kImgRow, (int)(reinterpret_cast<uintptr_t>(mrow) & 15) + kLanePx * lane, mv[b]);
+                } else {
+                    const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + b * kImgRow + lane * 16);
+                    mv[b][0] = q4.x; mv[b][1] = q4.y; mv[b][2] = q4.z; mv[b][3] = q4.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    sm[b] = (int)__dp4a(GEN ? (mv[b][q] & keep_mask(nval, q)) : mv[b][q], 0x01010101u, (unsigned)sm[b]);
             }
             if (!full) continue;
-            const uint4 *r0 = reinterpret_cast<const uint4 *>(slot + NB * 512 + lane * 32);
-            const uint4 *r1 = reinterpret_cast<const uint4 *>(slot + NB * 512 + 1024 + lane * 32);
-            const uint4 a0 = r0[0], a1 = r0[1], b0 = r1[0], b1 = r1[1];
+            uint32_t r0[8], r1[8];
+            if (GEN) {
+                read_words<8>(slot + NB * kImgRow,
+                              (int)(reinterpret_cast<uintptr_t>(pan + (2 * i) * W + 2 * j0) & 15) + 2 * kLanePx * lane, r0);
+                read_words<8>(slot + NB * kImgRow + PR,
+                              (int)(reinterpret_cast<uintptr_t>(pan + (2 * i + 1) * W + 2 * j0) & 15) + 2 * kLanePx * lane, r1);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(slot + NB * kImgRow + lane * 32 + 16 * k);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(slot + NB * kImgRow + PR + lane * 32 + 16 * k);
+                    r0[4 * k] = u.x; r0[4 * k + 1] = u.y; r0[4 * k + 2] = u.z; r0[4 * k + 3] = u.w;
+                    r1[4 * k] = v.x; r1[4 * k + 1] = v.y; r1[4 * k + 2] = v.z; r1[4 * k + 3] = v.w;
+                }
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 // PAN words of rows 2i, 2i+1 covering MS pixels 4q .. 4q+3
-                const uint32_t ua = q == 0 ? a0.x : q == 1 ? a0.z : q == 2 ? a1.x : a1.z;
-                const uint32_t ub = q == 0 ? a0.y : q == 1 ? a0.w : q == 2 ? a1.y : a1.w;
-                const uint32_t la = q == 0 ? b0.x : q == 1 ? b0.z : q == 2 ? b1.x : b1.z;
-                const uint32_t lb = q == 0 ? b0.y : q == 1 ? b0.w : q == 2 ? b1.y : b1.w;
+                const uint32_t ua = r0[2 * q], ub = r0[2 * q + 1], la = r1[2 * q], lb = r1[2 * q + 1];
                 int z[4];
                 z[0] = (int)__dp4a(__byte_perm(ua, la, 0x5410u), 0x01010101u, 0u) - 512;
                 z[1] = (int)__dp4a(__byte_perm(ua, la, 0x7632u), 0x01010101u, 0u) - 512;
@@ -582,8 +724,7 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
                 z[3] = (int)__dp4a(__byte_perm(ub, lb, 0x7632u), 0x01010101u, 0u) - 512;
                 int v[NB];
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    v[b] = (int)((q == 0 ? mv[b].x : q == 1 ? mv[b].y : q == 2 ? mv[b].z : mv[b].w) ^ 0x80808080u);
+                for (int b = 0; b < NB; ++b) v[b] = (int)(mv[b][q] ^ 0x80808080u);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     s1[b] = __dp4a(v[b], 0x01010101, s1[b]);
@@ -611,7 +752,7 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
         cp_async_wait<0>();
 #pragma unroll
         for (int b = 0; b < NB; ++b) sum_tot[b] += (double)(unsigned)sm[b];
-        if (!__any_sync(0xffffffffu, full)) continue;
+        if (!any_full) continue;
         int S1[K], S2[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -823,21 +964,25 @@ struct FastFn {
     const void *fn;
     int smem;
 };
-template <int NB>
-FastFn pan_u8_fn() { return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB>), FastPan<NB>::kSmem}; }
-template <int NB>
-FastFn ms_u8_fn() { return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB>), FastMs<NB>::kSmem}; }
-FastFn fast_fn(bool ms_pass, int nb) {
+template <int NB, bool GEN>
+FastFn pan_u8_fn() { return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB, GEN>), FastPan<NB>::kSmem}; }
+template <int NB, bool GEN>
+FastFn ms_u8_fn() { return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB, GEN>), FastMs<NB>::kSmem}; }
+template <bool GEN>
+FastFn fast_fn_g(bool ms_pass, int nb) {
     switch (nb) {
-        case 1: return ms_pass ? ms_u8_fn<1>() : pan_u8_fn<1>();
-        case 2: return ms_pass ? ms_u8_fn<2>() : pan_u8_fn<2>();
-        case 3: return ms_pass ? ms_u8_fn<3>() : pan_u8_fn<3>();
-        case 4: return ms_pass ? ms_u8_fn<4>() : pan_u8_fn<4>();
-        case 5: return ms_pass ? ms_u8_fn<5>() : pan_u8_fn<5>();
-        case 6: return ms_pass ? ms_u8_fn<6>() : pan_u8_fn<6>();
-        case 7: return ms_pass ? ms_u8_fn<7>() : pan_u8_fn<7>();
-        default: return ms_pass ? ms_u8_fn<8>() : pan_u8_fn<8>();
+        case 1: return ms_pass ? ms_u8_fn<1, GEN>() : pan_u8_fn<1, GEN>();
+        case 2: return ms_pass ? ms_u8_fn<2, GEN>() : pan_u8_fn<2, GEN>();
+        case 3: return ms_pass ? ms_u8_fn<3, GEN>() : pan_u8_fn<3, GEN>();
+        case 4: return ms_pass ? ms_u8_fn<4, GEN>() : pan_u8_fn<4, GEN>();
+        case 5: return ms_pass ? ms_u8_fn<5, GEN>() : pan_u8_fn<5, GEN>();
+        case 6: return ms_pass ? ms_u8_fn<6, GEN>() : pan_u8_fn<6, GEN>();
+        case 7: return ms_pass ? ms_u8_fn<7, GEN>() : pan_u8_fn<7, GEN>();
+        default: return ms_pass ? ms_u8_fn<8, GEN>() : pan_u8_fn<8, GEN>();
     }
+}
+FastFn fast_fn(bool ms_pass, int nb, bool aligned) {
+    return aligned ? fast_fn_g<false>(ms_pass, nb) : fast_fn_g<true>(ms_pass, nb);
 }
 
 // Grid of a fast-path kernel: one 256-thread CTA per SM (the row rings use
@@ -904,7 +1049,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     a.a4_fused = m.a4_fused;
     a.a4_in = m.a4_in;
     a.stride = kMetricStride;
-    const bool fast = !m.fused_f32 && !m.in_f32 && m.a16;
+    const bool fast = !m.fused_f32 && !m.in_f32;
     double *out = m.workspace;
     double *pan_part = m.workspace + 8;
     double *ms_part = pan_part + (int64_t)kMetricMaxCtas * kMetricStride;
@@ -912,7 +1057,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     cudaError_t e;
     // PAN-resolution pass
     if (fast) {
-        const FastFn fp = fast_fn(false, m.bands);
+        const FastFn fp = fast_fn(false, m.bands, m.a16 != 0);
         const int64_t items = ((m.W + kStrip - 1) / kStrip) * ((m.H + kWin - 1) / kWin);
         e = fast_grid(fp, items, &gp);
         if (e != cudaSuccess) return e;
@@ -934,8 +1079,8 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     MetricArgs b = a;
     b.partial = ms_part;
     void *args2[] = {&b};
-    if (!m.in_f32 && m.a32_ms) {
-        const FastFn fm = fast_fn(true, m.bands);
+    if (!m.in_f32) {
+        const FastFn fm = fast_fn(true, m.bands, m.a32_ms != 0);
         const int64_t items = ((m.W / 2 + kStrip - 1) / kStrip) * ((m.H / 2 + kWin - 1) / kWin);
         e = fast_grid(fm, items, &gm);
         if (e != cudaSuccess) return e;

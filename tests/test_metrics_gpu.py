@@ -50,7 +50,9 @@ def check(got, ref, f32):
 @pytest.mark.parametrize("wav", [0, 1])
 @pytest.mark.parametrize("shape,B", [((64, 64), 3), ((128, 192), 6), ((130, 258), 4),
                                      ((200, 136), 8), ((96, 512), 1), ((66, 70), 2),
-                                     ((96, 1056), 5), ((160, 528), 7), ((64, 80), 2)])
+                                     ((96, 1056), 5), ((160, 528), 7), ((64, 80), 2),
+                                     ((96, 610), 6), ((64, 534), 8), ((130, 4070), 3),
+                                     ((72, 1048), 4)])
 def test_metrics_u8_product(wav, shape, B, ws):
     H, W = shape
     pan, ms = scenegen.make_scene(H, W, B, seed=H + W + B)
@@ -82,11 +84,11 @@ def _offset_copy(t, off):
     return buf[off:].view(t.shape)
 
 
-@pytest.mark.parametrize("W", [544, 1056])
-def test_u8_fast_paths_equal_generic_paths(W, ws):
-    """The 16-pixel-per-lane cp.async paths (W % 16 == 0 / W % 32 == 0, aligned
-    planes) and the generic 4-pixel paths (the same data at an odd byte offset)
-    agree on the same product."""
+@pytest.mark.parametrize("W", [544, 1056, 610])
+def test_u8_aligned_and_misaligned_planes_agree(W, ws):
+    """The 8-bit paths stage 16-byte chunks and shift rows into place; planes at
+    odd byte offsets (MS bands starting mid-chunk, copied byte by byte at the
+    plane start) give the same figures as aligned planes."""
     H, B = 96, 4
     pan, ms = scenegen.make_scene(H, W, B, seed=9)
     pan, ms = pan.to(DEV), ms.to(DEV)
@@ -94,6 +96,20 @@ def test_u8_fast_paths_equal_generic_paths(W, ws):
     fast = gpu_metrics(u8, ms, pan, ws)
     slow = gpu_metrics(_offset_copy(u8, 2), [_offset_copy(m, 1) for m in ms], pan, ws)
     np.testing.assert_allclose(fast, slow, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("W", [512, 614])
+def test_u8_path_equals_float_path(W, ws):
+    """The same integer-valued product through the 8-bit (dp4a) path and the
+    float path: equal within the float path's bar."""
+    H, B = 96, 5
+    pan, ms = scenegen.make_scene(H, W, B, seed=12)
+    pan, ms = pan.to(DEV), ms.to(DEV)
+    _, u8 = fuse(pan, ms, 1, f32=False, u8=True)
+    a = gpu_metrics(u8, ms, pan, ws)
+    b = gpu_metrics(u8.float(), ms.float(), pan.float(), ws)
+    assert abs(a[0] - b[0]) <= 1e-6 * a[0]
+    assert np.abs(a[1:] - b[1:]).max() <= 2e-5
 
 
 def test_sync_entry_points_agree(ws):
