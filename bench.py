@@ -522,6 +522,34 @@ def measure_config4(args, dev, peak: float) -> dict:
     }
 
 
+def measure_transforms(args, dev, peak: float) -> dict:
+    """Standalone one-level 2D DWT and inverse at the benchmark size (D4 and Haar)."""
+    import torch
+
+    from paper_1803_00737_gb300 import _C
+    S = 4096 if args.forms_small else 16384
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    img = torch.randint(0, 256, (S, S), generator=g, device=dev, dtype=torch.uint8)
+    Z = torch.empty((S, S), dtype=torch.float32, device=dev)
+    out = torch.empty((S, S), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {"workload": f"PAN {S}x{S}: uint8 image -> float coefficients (dwt2), float coefficients "
+                       "-> float image (idwt2)"}
+    for wav, name in ((1, "d4"), (0, "haar")):
+        t_f = _time_ms(lambda: _C.dwtfuse_dwt2(img, wav, Z), max(3, args.form_reps), stream) / 1e3
+        t_i = _time_ms(lambda: _C.dwtfuse_idwt2(Z, wav, out), max(3, args.form_reps), stream) / 1e3
+        px = S * S
+        res[name] = {
+            "dwt2_gpxs": px / t_f / 1e9, "idwt2_gpxs": px / t_i / 1e9,
+            "dwt2_roofline": {"achieved": 5.0 * px / t_f / 1e9, "frac": 5.0 * px / t_f / 1e9 / peak},
+            "idwt2_roofline": {"achieved": 8.0 * px / t_i / 1e9, "frac": 8.0 * px / t_i / 1e9 / peak},
+        }
+    del img, Z, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args) -> None:
     import torch
 
@@ -625,6 +653,7 @@ def run_ours(args) -> None:
         torch.cuda.empty_cache()
         forms = measure_forms(args, dev, peak, world)
         forms["config4"] = measure_config4(args, dev, peak)
+        forms["transforms"] = measure_transforms(args, dev, peak)
 
     if rank == 0:
         print(json.dumps({

@@ -85,6 +85,41 @@ int dwtfuse_fuse(const void *pan, const void *const *ms, int bands, int64_t H, i
                  int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *stream);
 
 /*
+ * dwtfuse_fuse with an explicit LL replacement gain: LL <- ll_gain * MS_b.
+ * The paper (Sec. 2) does not state the gain; dwtfuse_fuse uses the DC gain
+ * of the 2D low-pass (1 Haar, 2 D4).  ll_gain = 1 for D4 replaces the
+ * approximation by the raw MS values, one reading of the paper's weak D4
+ * quality figures (Table 3).  ll_gain must be finite, else DWTFUSE_EINVAL.
+ */
+int dwtfuse_fuse_ex(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                    int wavelet, int in_dtype, float ll_gain, float *out_f32, uint8_t *out_u8,
+                    void *stream);
+
+/*
+ * One-level 2D DWT of an image (Sec. 2: 1D transform of every row, then of
+ * every column; Haar Eq. 1-2, Daubechies-4 Eq. 3-10 with periodic wrap), the
+ * transform the fusion applies before the LL replacement.
+ *   img     H x W, in_dtype (uint8 or float)
+ *   coeffs  H x W float, the paper's in-place layout: with A / D the row
+ *           approximation / detail and a column pass of low-pass then
+ *           high-pass, top-left = LL (low-pass of A), top-right = low-pass of D,
+ *           bottom-left = high-pass of A, bottom-right = high-pass of D.
+ * The D4 detail filter is the quadrature mirror (h3, -h2, h1, -h0) of Eq. 7-8's h
+ * (Eq. 9-10 as printed do not invert).  coeffs must be 8-byte aligned.
+ */
+int dwtfuse_dwt2(const void *img, int in_dtype, int64_t H, int64_t W, int wavelet, float *coeffs,
+                 void *stream);
+
+/*
+ * Inverse one-level 2D DWT (Sec. 2: columns, then rows; Haar Eq. 11-12, D4
+ * Eq. 13-16) of a coefficient image in the layout of dwtfuse_dwt2, into a float
+ * image and/or a uint8 image (clamped, rounded half to even); at least one
+ * output.  dwtfuse_idwt2(dwtfuse_dwt2(x)) = x up to rounding.
+ */
+int dwtfuse_idwt2(const float *coeffs, int64_t H, int64_t W, int wavelet, float *out_f32,
+                  uint8_t *out_u8, void *stream);
+
+/*
  * Adjoint (vector-Jacobian product) of dwtfuse_fuse with respect to PAN and
  * every MS band, for float images.  With U and LL as above and S the
  * synthesis matrix (S = A^T for D4, S = 2 A^T for the /2 Haar of Eq. 1-2, so

@@ -68,6 +68,7 @@ def _load():
                 "oracle_fuse_adjoint": (i, [i, l, l, i, d, _D, _D, ctypes.POINTER(_D)]),
                 "oracle_fuse_points": (i, [i, l, l, d, _D, _U8, _D, _U8, l, _L, _L, _D]),
                 "oracle_to_u8": (None, [l, _D, _U8]),
+                "oracle_dwt2_points": (i, [i, l, l, _D, _U8, l, _L, _L, _D]),
                 "oracle_ergas_t": (d, [l, l, i, _V, i, ctypes.POINTER(_V), i]),
                 "oracle_q_index_t": (d, [l, l, _V, i, _V, i, l]),
                 "oracle_qnr_t": (i, [l, l, i, _V, i, ctypes.POINTER(_V), i, _V, i, l,
@@ -231,6 +232,25 @@ def fuse_points(pan, ms_band, wavelet: int, ys, xs, gain: float | None = None) -
     _check(_load().oracle_fuse_points(int(wavelet), H, W, ctypes.c_double(g), pd, pu, md, mu,
                                       ys.size, ys.ctypes.data_as(_L), xs.ctypes.data_as(_L),
                                       _p(out)), "fuse_points")
+    return out
+
+
+def dwt2_points(img, wavelet: int, is_, js) -> np.ndarray:
+    """Forward 2D transform coefficients at (is_[k], js_[k]) of an (H, W) uint8
+    or float image, evaluated from the tap lists."""
+    H, W = img.shape
+    is_ = np.ascontiguousarray(is_, dtype=np.int64)
+    js = np.ascontiguousarray(js, dtype=np.int64)
+    out = np.empty(is_.size)
+    if img.dtype == np.uint8:
+        a = np.ascontiguousarray(img)
+        rc = _load().oracle_dwt2_points(int(wavelet), H, W, None, a.ctypes.data_as(_U8), is_.size,
+                                        is_.ctypes.data_as(_L), js.ctypes.data_as(_L), _p(out))
+    else:
+        a = _f64(img)
+        rc = _load().oracle_dwt2_points(int(wavelet), H, W, _p(a), None, is_.size,
+                                        is_.ctypes.data_as(_L), js.ctypes.data_as(_L), _p(out))
+    _check(rc, "dwt2_points")
     return out
 
 

@@ -435,6 +435,26 @@ int oracle_fuse_points(int kind, long H, long W, double gain, const double *pan,
     return 0;
 }
 
+/* Coefficients of the forward 2D transform (rows, then columns) at n sampled
+ * indices (is[k], js[k]) of the H x W coefficient image, from the same tap
+ * lists (for images too large for the whole-image oracle). */
+int oracle_dwt2_points(int kind, long H, long W, const double *img, const uint8_t *img_u8, long n,
+                       const long *is, const long *js, double *out) {
+    if (check_shape(kind, H, W)) return 1;
+    if (!img == !img_u8) return 1;
+    wavelet_t w = make_wavelet(kind, NULL);
+    point_ctx c = {&w, H, W, 0.0, img, img_u8, NULL, NULL};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < n; ++k) {
+        long idx[4];
+        double wt[4], acc = 0.0;
+        const int nt = fwd1d_taps(c.w, H, is[k], idx, wt);
+        for (int t = 0; t < nt; ++t) acc += wt[t] * row_fwd(&c, idx[t], js[k]);
+        out[k] = acc;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------ uint8 output */
 
 /* Reading R6: clamp to [0, 255], then round half to even. */

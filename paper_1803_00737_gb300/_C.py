@@ -57,6 +57,10 @@ _SIGS = {
     "dwtfuse_version": (_i, []),
     "dwtfuse_last_cuda_error": (_i, []),
     "dwtfuse_fuse": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp]),
+    "dwtfuse_fuse_ex": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, ctypes.c_float, _vp, _vp,
+                             _vp]),
+    "dwtfuse_dwt2": (_i, [_vp, _i, _i64, _i64, _i, _vp, _vp]),
+    "dwtfuse_idwt2": (_i, [_vp, _i64, _i64, _i, _vp, _vp, _vp]),
     "dwtfuse_fuse_backward": (_i, [_vp, _i, _i64, _i64, _i, _vp, ctypes.POINTER(_vp), _vp]),
     "dwtfuse_batched_workspace_size": (_sz, []),
     "dwtfuse_fuse_batched": (_i, [ctypes.POINTER(Scene), _i, _vp, _sz, _i, _i, _vp]),
@@ -152,6 +156,42 @@ def dwtfuse_fuse(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | No
                             _dev(out_u8, "out_u8") if out_u8 is not None else None,
                             _stream(stream))
     _check(st, "dwtfuse_fuse")
+
+
+def dwtfuse_fuse_ex(pan: torch.Tensor, ms, wavelet: int, ll_gain: float,
+                    out_f32: torch.Tensor | None = None, out_u8: torch.Tensor | None = None,
+                    stream=None) -> None:
+    """dwtfuse_fuse with an explicit LL replacement gain."""
+    bands = _bands(ms)
+    H, W = pan.shape
+    ptrs = (_vp * len(bands))(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
+    st = lib().dwtfuse_fuse_ex(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet),
+                               _dtype_code(pan, "pan"), float(ll_gain),
+                               _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                               _dev(out_u8, "out_u8") if out_u8 is not None else None,
+                               _stream(stream))
+    _check(st, "dwtfuse_fuse_ex")
+
+
+def dwtfuse_dwt2(img: torch.Tensor, wavelet: int, coeffs: torch.Tensor, stream=None) -> None:
+    """One-level 2D DWT (rows, then columns) into a float coefficient image."""
+    H, W = img.shape
+    if coeffs.dtype != torch.float32 or tuple(coeffs.shape) != (H, W):
+        raise ValueError(f"coeffs must be float32 of shape ({H}, {W})")
+    _check(lib().dwtfuse_dwt2(_dev(img, "img"), _dtype_code(img, "img"), H, W, int(wavelet),
+                              _dev(coeffs, "coeffs"), _stream(stream)), "dwtfuse_dwt2")
+
+
+def dwtfuse_idwt2(coeffs: torch.Tensor, wavelet: int, out_f32: torch.Tensor | None = None,
+                  out_u8: torch.Tensor | None = None, stream=None) -> None:
+    """Inverse one-level 2D DWT (columns, then rows) into float and/or uint8 images."""
+    H, W = coeffs.shape
+    if coeffs.dtype != torch.float32:
+        raise TypeError("coeffs must be float32")
+    _check(lib().dwtfuse_idwt2(_dev(coeffs, "coeffs"), H, W, int(wavelet),
+                               _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                               _dev(out_u8, "out_u8") if out_u8 is not None else None,
+                               _stream(stream)), "dwtfuse_idwt2")
 
 
 def dwtfuse_fuse_backward(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.Tensor,

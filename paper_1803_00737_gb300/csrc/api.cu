@@ -150,6 +150,58 @@ int dwtfuse_fuse(const void *pan, const void *const *ms, int bands, int64_t H, i
     return cuda_status(launch_fuse(s, rows_per_item(), 0, static_cast<cudaStream_t>(stream)));
 }
 
+int dwtfuse_fuse_ex(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                    int wavelet, int in_dtype, float ll_gain, float *out_f32, uint8_t *out_u8,
+                    void *stream) {
+    if (!(ll_gain == ll_gain) || ll_gain > 3.4e38f || ll_gain < -3.4e38f) return DWTFUSE_EINVAL;
+    SceneArgs s;
+    const int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
+    if (st != DWTFUSE_OK) return st;
+    s.gain = ll_gain;
+    return cuda_status(launch_fuse(s, rows_per_item(), 0, static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_dwt2(const void *img, int in_dtype, int64_t H, int64_t W, int wavelet, float *coeffs,
+                 void *stream) {
+    if (!img || !coeffs) return DWTFUSE_EINVAL;
+    if (in_dtype != DWTFUSE_U8 && in_dtype != DWTFUSE_F32) return DWTFUSE_EINVAL;
+    const int st = check_shape(H, W, wavelet);
+    if (st != DWTFUSE_OK) return st;
+    const uintptr_t es = in_dtype == DWTFUSE_F32 ? 4 : 1;
+    if (!aligned(img, 2 * es) || !aligned(coeffs, 8)) return DWTFUSE_EALIGN;
+    DwtLaunch d{};
+    d.src = img;
+    d.dst_f32 = coeffs;
+    d.H = H;
+    d.W = W;
+    d.wavelet = wavelet;
+    d.in_f32 = in_dtype == DWTFUSE_F32;
+    d.a4 = (W % 4 == 0) && aligned(img, 4 * es);
+    d.pairs = ((W / 2) % 2) == 0;
+    d.rows = rows_per_item();
+    return cuda_status(launch_dwt2(d, static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_idwt2(const float *coeffs, int64_t H, int64_t W, int wavelet, float *out_f32,
+                  uint8_t *out_u8, void *stream) {
+    if (!coeffs || (!out_f32 && !out_u8)) return DWTFUSE_EINVAL;
+    const int st = check_shape(H, W, wavelet);
+    if (st != DWTFUSE_OK) return st;
+    if (!aligned(coeffs, 4) || (out_f32 && !aligned(out_f32, 8)) || (out_u8 && !aligned(out_u8, 2)))
+        return DWTFUSE_EALIGN;
+    DwtLaunch d{};
+    d.src = coeffs;
+    d.dst_f32 = out_f32;
+    d.dst_u8 = out_u8;
+    d.H = H;
+    d.W = W;
+    d.wavelet = wavelet;
+    d.inverse = 1;
+    d.a4 = (W % 4 == 0) && (!out_f32 || aligned(out_f32, 16)) && (!out_u8 || aligned(out_u8, 4));
+    d.rows = rows_per_item();
+    return cuda_status(launch_dwt2(d, static_cast<cudaStream_t>(stream)));
+}
+
 int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W, int wavelet,
                           float *grad_pan, float *const *grad_ms, void *stream) {
     if (!grad_out || !grad_pan || !grad_ms) return DWTFUSE_EINVAL;

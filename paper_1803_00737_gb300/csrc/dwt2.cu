@@ -1,0 +1,265 @@
+// Standalone one-level 2D DWT and inverse (the transforms either side of the
+// LL replacement, Sec. 2): forward = 1D transform of every row, then of every
+// column (Haar Eq. 1-2, D4 Eq. 3-10 with periodic wrap); inverse = columns,
+// then rows (Haar Eq. 11-12, D4 Eq. 13-16).  The coefficient image Z is H x W
+// float in the paper's in-place layout: with A / D the row approximation /
+// detail and a column pass of low-pass (h) then high-pass (g),
+//     Z(m, j)           = sum_a h_a A(2m+a, j)    (LL, top-left)
+//     Z(m, W/2 + j)     = sum_a h_a D(2m+a, j)    (top-right)
+//     Z(H/2 + m, j)     = sum_a g_a A(2m+a, j)    (bottom-left)
+//     Z(H/2 + m, W/2+j) = sum_a g_a D(2m+a, j)    (bottom-right)
+// D4: h of Eq. 7-8, g = (h3, -h2, h1, -h0) (the quadrature mirror; Eq. 9-10
+// as printed do not invert).  The D4 synthesis is the transpose of the
+// analysis; the /2 Haar synthesis is twice its transpose.
+//
+// Same warp strips as the fused kernels: a lane owns image columns x..x+3
+// (coefficient columns n, n+1 of each half) and walks down R coefficient rows
+// with a sliding window of image rows (forward) or coefficient rows (inverse).
+#include "fuse_tile.cuh"
+#include "launch.h"
+
+namespace dwtfuse {
+
+constexpr int kDwtThreads = 256;
+constexpr int kDwtWarps = kDwtThreads / 32;
+// Detail filter g = (h3, -h2, h1, -h0).
+constexpr float kG0 = kH3, kG1 = -kH2, kG2 = kH1, kG3 = -kH0;
+
+struct DwtArgs {
+    const void *src;  // image (forward, u8 or f32) or coefficients (inverse, f32)
+    float *dst_f32;   // coefficients (forward) or image (inverse)
+    uint8_t *dst_u8;  // image (inverse only), optional
+    int64_t H, W;
+    int32_t a4;       // W % 4 == 0 and aligned for 4-pixel image vectors
+    int32_t pairs;    // W/2 even: coefficient pairs are 8-byte aligned in both halves
+};
+
+// Two coefficients (columns n, n+1) of one coefficient row; n+1 only if `two`.
+__device__ __forceinline__ void store_pair(float *p, bool pair, bool two, float a, float b) {
+    if (pair) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    } else {
+        p[0] = a;
+        if (two) p[1] = b;
+    }
+}
+
+// Row analysis of one image row at coefficient columns n, n+1 (pixels x..x+5 = v[2..7]).
+__device__ __forceinline__ void d4_row_ad(const float *v, float *ra, float *rd) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float *s = v + 2 + 2 * j;
+        ra[j] = fmaf(kH3, s[3], fmaf(kH2, s[2], fmaf(kH1, s[1], kH0 * s[0])));
+        rd[j] = fmaf(kG3, s[3], fmaf(kG2, s[2], fmaf(kG1, s[1], kG0 * s[0])));
+    }
+}
+
+template <typename T, int WAV>
+__device__ __forceinline__ void dwt2_item(const DwtArgs &s, int64_t x0, int64_t m_s, int64_t m_e, int lane) {
+    const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1;
+    const LaneCols c = lane_cols(x0, lane, W);
+    const bool a4 = s.a4 != 0, pair = s.pairs != 0;
+    const T *img = static_cast<const T *>(s.src);
+    float *Z = s.dst_f32;
+    if (WAV == 0) {
+        for (int64_t m = m_s; m < m_e; ++m) {
+            float p0[4], p1[4];
+            load_row4(img + (2 * m) * W, c, a4, p0);
+            load_row4(img + (2 * m + 1) * W, c, a4, p1);
+            if (!c.active) continue;
+            float A0[2], D0[2], A1[2], D1[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {  // Eq. 1-2 along the rows
+                A0[j] = (p0[2 * j] + p0[2 * j + 1]) * 0.5f;
+                D0[j] = (p0[2 * j] - p0[2 * j + 1]) * 0.5f;
+                A1[j] = (p1[2 * j] + p1[2 * j + 1]) * 0.5f;
+                D1[j] = (p1[2 * j] - p1[2 * j + 1]) * 0.5f;
+            }
+            // Eq. 1-2 along the columns
+            store_pair(Z + m * W + c.nB, pair, c.two, (A0[0] + A1[0]) * 0.5f, (A0[1] + A1[1]) * 0.5f);
+            store_pair(Z + m * W + W2 + c.nB, pair, c.two, (D0[0] + D1[0]) * 0.5f, (D0[1] + D1[1]) * 0.5f);
+            store_pair(Z + (H2 + m) * W + c.nB, pair, c.two, (A0[0] - A1[0]) * 0.5f, (A0[1] - A1[1]) * 0.5f);
+            store_pair(Z + (H2 + m) * W + W2 + c.nB, pair, c.two, (D0[0] - D1[0]) * 0.5f, (D0[1] - D1[1]) * 0.5f);
+        }
+        return;
+    }
+    // D4: rows 2m .. 2m+3 (periodic) feed coefficient row m.
+    float a0[2], d0[2], a1[2], d1[2];
+    {
+        float v[8];
+        load_row8(img + (2 * m_s) * W, c, a4, v);
+        d4_row_ad(v, a0, d0);
+        load_row8(img + (2 * m_s + 1) * W, c, a4, v);
+        d4_row_ad(v, a1, d1);
+    }
+    for (int64_t m = m_s; m < m_e; ++m) {
+        float va[8], vb[8];
+        load_row8(img + wrap(2 * m + 2, H) * W, c, a4, va);
+        load_row8(img + wrap(2 * m + 3, H) * W, c, a4, vb);
+        float a2[2], d2[2], a3[2], d3[2];
+        d4_row_ad(va, a2, d2);
+        d4_row_ad(vb, a3, d3);
+        if (c.active) {
+            float ll[2], lh[2], hl[2], hh[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                ll[j] = fmaf(kH3, a3[j], fmaf(kH2, a2[j], fmaf(kH1, a1[j], kH0 * a0[j])));
+                lh[j] = fmaf(kG3, a3[j], fmaf(kG2, a2[j], fmaf(kG1, a1[j], kG0 * a0[j])));
+                hl[j] = fmaf(kH3, d3[j], fmaf(kH2, d2[j], fmaf(kH1, d1[j], kH0 * d0[j])));
+                hh[j] = fmaf(kG3, d3[j], fmaf(kG2, d2[j], fmaf(kG1, d1[j], kG0 * d0[j])));
+            }
+            store_pair(Z + m * W + c.nB, pair, c.two, ll[0], ll[1]);
+            store_pair(Z + m * W + W2 + c.nB, pair, c.two, hl[0], hl[1]);
+            store_pair(Z + (H2 + m) * W + c.nB, pair, c.two, lh[0], lh[1]);
+            store_pair(Z + (H2 + m) * W + W2 + c.nB, pair, c.two, hh[0], hh[1]);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            a0[j] = a2[j]; d0[j] = d2[j];
+            a1[j] = a3[j]; d1[j] = d3[j];
+        }
+    }
+}
+
+// Inverse.  Per coefficient row i the lane forms, at its 4 image columns,
+//   RA(i, .) = row synthesis of (LL, top-right) and RB(i, .) = of (bottom-left, HH),
+// then column synthesis mixes rows i = m and m-1 (D4) or row m alone (Haar).
+__device__ __forceinline__ void load_coef3(const float *row, const LaneCols &c, float *v) {
+    v[0] = __ldg(row + c.nA);
+    v[1] = __ldg(row + c.nB);
+    v[2] = __ldg(row + c.nC);
+}
+
+// D4 row synthesis at image columns x..x+3 of a low-pass half L (h taps) and
+// high-pass half G (g taps), each given at coefficient columns n-1, n, n+1.
+__device__ __forceinline__ void d4_row_syn(const float *L, const float *G, float *r) {
+    r[0] = fmaf(kG0, G[1], fmaf(kG2, G[0], fmaf(kH0, L[1], kH2 * L[0])));
+    r[1] = fmaf(kG1, G[1], fmaf(kG3, G[0], fmaf(kH1, L[1], kH3 * L[0])));
+    r[2] = fmaf(kG0, G[2], fmaf(kG2, G[1], fmaf(kH0, L[2], kH2 * L[1])));
+    r[3] = fmaf(kG1, G[2], fmaf(kG3, G[1], fmaf(kH1, L[2], kH3 * L[1])));
+}
+
+template <int WAV>
+__device__ __forceinline__ void idwt2_item(const DwtArgs &s, int64_t x0, int64_t m_s, int64_t m_e, int lane) {
+    const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
+    const LaneCols c = lane_cols(x0, lane, W);
+    const bool a4 = s.a4 != 0;
+    const float *Z = static_cast<const float *>(s.src);
+    OutPtrs o{s.dst_f32, s.dst_u8};
+    (void)HW;
+    if (WAV == 0) {
+        for (int64_t m = m_s; m < m_e; ++m) {
+            float ll[2], hl[2], lh[2], hh[2];
+            ll[0] = __ldg(Z + m * W + c.nB);              ll[1] = __ldg(Z + m * W + c.nC);
+            hl[0] = __ldg(Z + m * W + W2 + c.nB);         hl[1] = __ldg(Z + m * W + W2 + c.nC);
+            lh[0] = __ldg(Z + (H2 + m) * W + c.nB);       lh[1] = __ldg(Z + (H2 + m) * W + c.nC);
+            hh[0] = __ldg(Z + (H2 + m) * W + W2 + c.nB);  hh[1] = __ldg(Z + (H2 + m) * W + W2 + c.nC);
+            if (!c.active) continue;
+            // Eq. 11-12 on the columns, then on the rows
+            float v0[4], v1[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float ua = ll[j] + lh[j], ub = ll[j] - lh[j];  // rows 2m, 2m+1, approx column
+                const float da = hl[j] + hh[j], db = hl[j] - hh[j];  // rows 2m, 2m+1, detail column
+                v0[2 * j] = ua + da;
+                v0[2 * j + 1] = ua - da;
+                v1[2 * j] = ub + db;
+                v1[2 * j + 1] = ub - db;
+            }
+            store4(o, (2 * m) * W + c.x, a4, c.two, v0);
+            store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+        }
+        return;
+    }
+    float rap[4], rbp[4];  // RA, RB of coefficient row m-1
+    {
+        const int64_t mp = wrap(m_s - 1, H2);
+        float L[3], G[3];
+        load_coef3(Z + mp * W, c, L);
+        load_coef3(Z + mp * W + W2, c, G);
+        d4_row_syn(L, G, rap);
+        load_coef3(Z + (H2 + mp) * W, c, L);
+        load_coef3(Z + (H2 + mp) * W + W2, c, G);
+        d4_row_syn(L, G, rbp);
+    }
+    for (int64_t m = m_s; m < m_e; ++m) {
+        float L0[3], G0[3], L1[3], G1[3];
+        load_coef3(Z + m * W, c, L0);
+        load_coef3(Z + m * W + W2, c, G0);
+        load_coef3(Z + (H2 + m) * W, c, L1);
+        load_coef3(Z + (H2 + m) * W + W2, c, G1);
+        float ra[4], rb[4];
+        d4_row_syn(L0, G0, ra);
+        d4_row_syn(L1, G1, rb);
+        float v0[4], v1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // image row 2m: h0 RA(m) + h2 RA(m-1) + g0 RB(m) + g2 RB(m-1); row 2m+1: h1, h3, g1, g3
+            v0[q] = fmaf(kG2, rbp[q], fmaf(kG0, rb[q], fmaf(kH2, rap[q], kH0 * ra[q])));
+            v1[q] = fmaf(kG3, rbp[q], fmaf(kG1, rb[q], fmaf(kH3, rap[q], kH1 * ra[q])));
+            rap[q] = ra[q];
+            rbp[q] = rb[q];
+        }
+        if (c.active) {
+            store4(o, (2 * m) * W + c.x, a4, c.two, v0);
+            store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+        }
+    }
+}
+
+template <typename T, int WAV, bool INV>
+__global__ void __launch_bounds__(kDwtThreads, 2)
+dwt2_kernel(const __grid_constant__ DwtArgs s, int64_t strips_x, int64_t items, int R) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * kDwtWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kDwtWarps + (threadIdx.x >> 5); it < items; it += nwarps) {
+        const int64_t sx = it % strips_x, sy = it / strips_x;
+        const int64_t m_s = sy * R;
+        const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
+        if (INV)
+            idwt2_item<WAV>(s, sx * kWarpCols, m_s, m_e, lane);
+        else
+            dwt2_item<T, WAV>(s, sx * kWarpCols, m_s, m_e, lane);
+    }
+}
+
+namespace {
+
+const void *dwt_fn(bool inv, bool f32, int wav) {
+    if (inv) return wav ? reinterpret_cast<const void *>(&dwt2_kernel<float, 1, true>)
+                        : reinterpret_cast<const void *>(&dwt2_kernel<float, 0, true>);
+    if (f32) return wav ? reinterpret_cast<const void *>(&dwt2_kernel<float, 1, false>)
+                        : reinterpret_cast<const void *>(&dwt2_kernel<float, 0, false>);
+    return wav ? reinterpret_cast<const void *>(&dwt2_kernel<uint8_t, 1, false>)
+               : reinterpret_cast<const void *>(&dwt2_kernel<uint8_t, 0, false>);
+}
+
+}  // namespace
+
+cudaError_t launch_dwt2(const DwtLaunch &d, cudaStream_t stream) {
+    DwtArgs s{};
+    s.src = d.src;
+    s.dst_f32 = d.dst_f32;
+    s.dst_u8 = d.dst_u8;
+    s.H = d.H;
+    s.W = d.W;
+    s.a4 = d.a4;
+    s.pairs = d.pairs;
+    const void *fn = dwt_fn(d.inverse != 0, d.in_f32 != 0, d.wavelet);
+    int occ = 0, sms = 0;
+    cudaError_t e = resident_blocks(fn, kDwtThreads, &occ);
+    if (e != cudaSuccess) return e;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = (int64_t)sms * occ;
+    int R = d.rows > 0 ? d.rows : balanced_rows(d.H, d.W, cap * kDwtWarps);
+    const ItemGrid g = item_grid(d.H, d.W, R);
+    const int64_t need = (g.items + kDwtWarps - 1) / kDwtWarps;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    if (grid == 0) return cudaSuccess;
+    int64_t strips_x = g.strips_x, items = g.items;
+    void *args[] = {&s, &strips_x, &items, &R};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kDwtThreads), args, 0, stream);
+}
+
+}  // namespace dwtfuse

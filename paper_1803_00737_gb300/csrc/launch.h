@@ -67,6 +67,20 @@ inline int balanced_rows(int64_t H, int64_t W, int64_t warps) {
     return best;
 }
 
+// Standalone 2D DWT / inverse (dwt2.cu).
+struct DwtLaunch {
+    const void *src;   // image (forward) or coefficients (inverse)
+    float *dst_f32;    // coefficients (forward) or image (inverse), may be null for inverse
+    uint8_t *dst_u8;   // image (inverse), optional
+    int64_t H, W;
+    int32_t wavelet;
+    int32_t in_f32;    // forward: image is float (else uint8)
+    int32_t inverse;
+    int32_t a4;        // 4-pixel image vectors allowed
+    int32_t pairs;     // coefficient pairs 8-byte aligned in both halves
+    int32_t rows;      // MS rows per work item (0 = balanced)
+};
+
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);
 // SM count of the current device (cached per device).
@@ -75,6 +89,7 @@ cudaError_t sm_count(int *out);
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream);
 cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
                                  float *gpan, float *const *gms, int R, cudaStream_t stream);
+cudaError_t launch_dwt2(const DwtLaunch &d, cudaStream_t stream);
 cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream);
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);

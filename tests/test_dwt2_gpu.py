@@ -1,0 +1,97 @@
+"""Standalone 2D DWT and inverse on the GPU against the oracle's literal
+Eq. 1-16 transforms (whose matrices are pinned to the textbook filter bank).
+Haar on 8-bit images is exact (multiples of 1/4); D4 coefficients of 0-255
+images are within 5e-4; inverse of random coefficients within 1e-4 of the
+coefficient scale; inverse(forward(x)) = x."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1803_00737_gb300 import _C
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+SHAPES = [(4, 4), (6, 18), (10, 6), (64, 128), (66, 258), (130, 250), (34, 814), (200, 384)]
+
+
+@pytest.mark.parametrize("wav", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_dwt2_matches_oracle(wav, shape):
+    rng = np.random.default_rng(hash(shape) % 1000)
+    img = rng.integers(0, 256, shape).astype(np.uint8)
+    Z = torch.empty(shape, device=DEV)
+    _C.dwtfuse_dwt2(torch.from_numpy(img).to(DEV), wav, Z)
+    torch.cuda.synchronize()
+    ref = O.dwt2(img.astype(np.float64), wav)
+    got = Z.cpu().numpy()
+    if wav == 0:
+        np.testing.assert_array_equal(got, ref.astype(np.float32))
+    else:
+        assert np.abs(got - ref).max() <= 5e-4
+
+
+@pytest.mark.parametrize("wav", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_idwt2_matches_oracle(wav, shape):
+    rng = np.random.default_rng(7 + hash(shape) % 1000)
+    Z = rng.normal(0, 50, shape).astype(np.float32)
+    out = torch.empty(shape, device=DEV)
+    _C.dwtfuse_idwt2(torch.from_numpy(Z).to(DEV), wav, out)
+    torch.cuda.synchronize()
+    ref = O.idwt2(Z.astype(np.float64), wav)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("wav", [0, 1])
+def test_round_trip_and_u8_output(wav):
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, (96, 136)).astype(np.uint8)
+    x = torch.from_numpy(img).to(DEV)
+    Z = torch.empty((96, 136), device=DEV)
+    _C.dwtfuse_dwt2(x, wav, Z)
+    f = torch.empty((96, 136), device=DEV)
+    u = torch.empty((96, 136), dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_idwt2(Z, wav, f, u)
+    torch.cuda.synchronize()
+    assert (f.cpu() - x.cpu().float()).abs().max().item() <= (0 if wav == 0 else 1e-3)
+    assert torch.equal(u.cpu(), x.cpu())
+
+
+def test_dwt2_float_input_and_fusion_consistency():
+    """Fusing = replacing the LL quadrant of dwtfuse_dwt2's output and inverting."""
+    rng = np.random.default_rng(4)
+    H, W = 64, 96
+    pan = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    ms = rng.integers(0, 256, (1, H // 2, W // 2)).astype(np.uint8)
+    Z = torch.empty((H, W), device=DEV)
+    _C.dwtfuse_dwt2(torch.from_numpy(pan).float().to(DEV), 1, Z)
+    Z[: H // 2, : W // 2] = 2.0 * torch.from_numpy(ms[0]).float().to(DEV)
+    out = torch.empty((H, W), device=DEV)
+    _C.dwtfuse_idwt2(Z, 1, out)
+    fused = torch.empty((1, H, W), device=DEV)
+    _C.dwtfuse_fuse(torch.from_numpy(pan).to(DEV), torch.from_numpy(ms).to(DEV), 1, fused, None)
+    torch.cuda.synchronize()
+    assert (out - fused[0]).abs().max().item() <= 5e-4
+
+
+def test_dwt2_full_size_sampled_and_round_trip():
+    """16384^2 uint8 image, D4: sampled coefficients of every quadrant against
+    the point-wise oracle, and inverse(forward(x)) = x at full size."""
+    H = W = 16384
+    g = torch.Generator(device=DEV)
+    g.manual_seed(0)
+    img = torch.randint(0, 256, (H, W), generator=g, device=DEV, dtype=torch.uint8)
+    Z = torch.empty((H, W), device=DEV)
+    _C.dwtfuse_dwt2(img, 1, Z)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    ii = np.concatenate([[0, H // 2 - 1, H // 2, H - 1], rng.integers(0, H, 400)])
+    jj = np.concatenate([[W - 1, 0, W // 2, W // 2 - 1], rng.integers(0, W, 400)])
+    ref = O.dwt2_points(img.cpu().numpy(), 1, ii, jj)
+    got = Z[torch.from_numpy(ii).to(DEV), torch.from_numpy(jj).to(DEV)].cpu().numpy()
+    assert np.abs(got - ref).max() <= 5e-4
+    back = torch.empty((H, W), dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_idwt2(Z, 1, None, back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, img)

@@ -192,6 +192,15 @@ def test_point_evaluator_matches_whole_image(wav):
     np.testing.assert_array_equal(pts, F.ravel())
 
 
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
+def test_dwt2_point_evaluator_matches_whole_image(wav):
+    H, W = 12, 10
+    img = RNG.integers(0, 256, (H, W)).astype(np.uint8)
+    Z = O.dwt2(img.astype(float), wav)
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    np.testing.assert_array_equal(O.dwt2_points(img, wav, ii.ravel(), jj.ravel()), Z.ravel())
+
+
 # ------------------------------------------------------------------ P8: adjoint
 
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
