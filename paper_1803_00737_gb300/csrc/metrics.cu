@@ -388,14 +388,18 @@ __device__ __forceinline__ uint32_t keep_mask(int v, int q) {
 constexpr int kLanePx = 16;
 constexpr int kStrip = 32 * kLanePx;
 constexpr int kWinPerStrip = kStrip / kWin;
-constexpr int kFastWarps = 8;
 constexpr int kImgRow = kStrip + 32;       // staged bytes per image row (alignment slack, 16-aligned)
 constexpr int kMsRow = kStrip / 2 + 32;    // staged bytes per MS row in the PAN pass
 
+// Warps per CTA and ring depth: up to 6 bands, 16 warps with a 2-row ring
+// (more warps hide the row-shifting work of unaligned widths and the state
+// fits 128 registers); 7-8 bands, 8 warps with a 3-row ring.
 template <int NB>
 struct FastPan {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
-    static constexpr int kStages = NB <= 6 ? 4 : 3;
+    static constexpr int kWarps = NB <= 6 ? 16 : 8;
+    static constexpr int kFastWarps = kWarps;
+    static constexpr int kStages = NB <= 6 ? 2 : 3;
     static constexpr int kRowBytes = K * kImgRow + NB * kMsRow;
     static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
                                  kFastWarps * NB * 8;
@@ -405,9 +409,10 @@ struct FastPan {
 // aligned planes): one chunk per lane and image, read back by the same lane.
 // GEN = true: any width and alignment, rows shifted into place.
 template <int NB, bool GEN>
-__global__ void __launch_bounds__(kFastWarps * 32, 1)
+__global__ void __launch_bounds__(FastPan<NB>::kWarps * 32, 1)
 metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     using C = FastPan<NB>;
+    constexpr int kFastWarps = C::kWarps;
     constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -594,7 +599,9 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
 template <int NB>
 struct FastMs {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
-    static constexpr int kStages = NB <= 6 ? 4 : 3;
+    static constexpr int kWarps = NB <= 6 ? 16 : 8;
+    static constexpr int kFastWarps = kWarps;
+    static constexpr int kStages = NB <= 6 ? 2 : 3;
     static constexpr int kPanRow = 2 * kStrip + 32;  // 32 PAN pixels per lane
     static constexpr int kRowBytes = NB * kImgRow + 2 * kPanRow;
     static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
@@ -607,9 +614,10 @@ struct FastMs {
 // integer multiply-adds.
 // GEN as for the PAN pass (aligned: W % 32 == 0, 16-byte aligned MS and PAN).
 template <int NB, bool GEN>
-__global__ void __launch_bounds__(kFastWarps * 32, 1)
+__global__ void __launch_bounds__(FastMs<NB>::kWarps * 32, 1)
 metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
     using C = FastMs<NB>;
+    constexpr int kFastWarps = C::kWarps;
     constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes, PR = C::kPanRow;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -963,11 +971,16 @@ const void *pan_fn_nb(int nb) {
 struct FastFn {
     const void *fn;
     int smem;
+    int warps;
 };
 template <int NB, bool GEN>
-FastFn pan_u8_fn() { return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB, GEN>), FastPan<NB>::kSmem}; }
+FastFn pan_u8_fn() {
+    return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB, GEN>), FastPan<NB>::kSmem, FastPan<NB>::kWarps};
+}
 template <int NB, bool GEN>
-FastFn ms_u8_fn() { return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB, GEN>), FastMs<NB>::kSmem}; }
+FastFn ms_u8_fn() {
+    return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB, GEN>), FastMs<NB>::kSmem, FastMs<NB>::kWarps};
+}
 template <bool GEN>
 FastFn fast_fn_g(bool ms_pass, int nb) {
     switch (nb) {
@@ -992,12 +1005,12 @@ cudaError_t fast_grid(const FastFn &f, int64_t items, int *grid) {
     cudaError_t e = cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem);
     if (e != cudaSuccess) return e;
     int occ = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f.fn, kFastWarps * 32, f.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f.fn, f.warps * 32, f.smem);
     if (e != cudaSuccess) return e;
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    int64_t g = (items + kFastWarps - 1) / kFastWarps;
+    int64_t g = (items + f.warps - 1) / f.warps;
     const int64_t cap = (int64_t)sms * occ;
     if (g > cap) g = cap;
     if (g > kMetricMaxCtas) g = kMetricMaxCtas;
@@ -1063,7 +1076,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
         if (e != cudaSuccess) return e;
         a.partial = pan_part;
         void *args[] = {&a};
-        e = cudaLaunchKernel(fp.fn, dim3(gp), dim3(kFastWarps * 32), args, fp.smem, stream);
+        e = cudaLaunchKernel(fp.fn, dim3(gp), dim3(fp.warps * 32), args, fp.smem, stream);
     } else {
         const void *fp = m.fused_f32 ? (m.in_f32 ? pan_fn_nb<float, float>(m.bands) : pan_fn_nb<float, uint8_t>(m.bands))
                                      : (m.in_f32 ? pan_fn_nb<uint8_t, float>(m.bands) : pan_fn_nb<uint8_t, uint8_t>(m.bands));
@@ -1084,7 +1097,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
         const int64_t items = ((m.W / 2 + kStrip - 1) / kStrip) * ((m.H / 2 + kWin - 1) / kWin);
         e = fast_grid(fm, items, &gm);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernel(fm.fn, dim3(gm), dim3(kFastWarps * 32), args2, fm.smem, stream);
+        e = cudaLaunchKernel(fm.fn, dim3(gm), dim3(fm.warps * 32), args2, fm.smem, stream);
     } else {
         const void *fm = m.in_f32 ? ms_fn_nb<float>(m.bands) : ms_fn_nb<uint8_t>(m.bands);
         const int64_t items = ((m.W / 2 + kWarpCols - 1) / kWarpCols) * ((m.H / 2 + kWin - 1) / kWin);
