@@ -107,8 +107,10 @@ int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int
     s->wavelet = wavelet;
     s->in_f32 = in_dtype == DWTFUSE_F32;
     s->gain = wavelet == DWTFUSE_D4 ? 2.0f : 1.0f;
-    s->a4 = (W % 4 == 0) && aligned(pan, 4 * es) && (!out_f32 || aligned(out_f32, 16)) &&
-            (!out_u8 || aligned(out_u8, 4));
+    const bool vec_ok = aligned(pan, 4 * es) && (!out_f32 || aligned(out_f32, 16)) &&
+                        (!out_u8 || aligned(out_u8, 4));
+    s->a4 = (W % 4 == 0) && vec_ok;
+    s->alt = (W % 4 == 2) && vec_ok;
     return DWTFUSE_OK;
 }
 

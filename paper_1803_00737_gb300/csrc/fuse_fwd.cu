@@ -7,16 +7,18 @@ namespace dwtfuse {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kAltMaxBands = 6;  // widest band chunk of the shifted-row instance
 
 // Single scene, bands [b0, b0 + NB).  Each warp takes work items
 // warp, warp + total_warps, ... (grid sized to the resident capacity).
-template <typename T, int WAV, int NB>
+// ALT: the instance for widths W % 4 == 2 with vector-aligned planes.
+template <typename T, int WAV, int NB, bool ALT>
 __global__ void __launch_bounds__(kThreads, 2)
 fuse_fwd_kernel(const __grid_constant__ SceneArgs s, int b0, int64_t strips_x, int64_t items, int R) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kWarps;
     for (int64_t it = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); it < items; it += nwarps)
-        run_item<T, WAV, NB>(s, it, strips_x, R, b0, NB, lane);
+        run_item<T, WAV, NB, ALT>(s, it, strips_x, R, b0, NB, lane);
 }
 
 // Batched: every warp pulls the next item index from `queue[0]`; item ranges
@@ -70,33 +72,45 @@ fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *qu
 namespace {
 
 template <typename T, int WAV, int NB>
-void *fwd_fn() { return reinterpret_cast<void *>(&fuse_fwd_kernel<T, WAV, NB>); }
+void *fwd_fn(bool alt) {
+    if constexpr (NB <= kAltMaxBands)
+        if (alt) return reinterpret_cast<void *>(&fuse_fwd_kernel<T, WAV, NB, true>);
+    return alt ? nullptr : reinterpret_cast<void *>(&fuse_fwd_kernel<T, WAV, NB, false>);
+}
 
 template <typename T, int WAV>
-void *fwd_fn_nb(int nb) {
+void *fwd_fn_nb(int nb, bool alt) {
     switch (nb) {
-        case 1: return fwd_fn<T, WAV, 1>();
-        case 2: return fwd_fn<T, WAV, 2>();
-        case 3: return fwd_fn<T, WAV, 3>();
-        case 4: return fwd_fn<T, WAV, 4>();
-        case 5: return fwd_fn<T, WAV, 5>();
-        case 6: return fwd_fn<T, WAV, 6>();
-        case 7: return fwd_fn<T, WAV, 7>();
-        default: return fwd_fn<T, WAV, 8>();
+        case 1: return fwd_fn<T, WAV, 1>(alt);
+        case 2: return fwd_fn<T, WAV, 2>(alt);
+        case 3: return fwd_fn<T, WAV, 3>(alt);
+        case 4: return fwd_fn<T, WAV, 4>(alt);
+        case 5: return fwd_fn<T, WAV, 5>(alt);
+        case 6: return fwd_fn<T, WAV, 6>(alt);
+        case 7: return fwd_fn<T, WAV, 7>(alt);
+        case 8: return fwd_fn<T, WAV, 8>(alt);
+        default: return nullptr;
     }
 }
 
-void *fwd_kernel_ptr(bool f32, int wav, int nb) {
-    if (f32) return wav ? fwd_fn_nb<float, 1>(nb) : fwd_fn_nb<float, 0>(nb);
-    return wav ? fwd_fn_nb<uint8_t, 1>(nb) : fwd_fn_nb<uint8_t, 0>(nb);
+void *fwd_kernel_ptr(bool f32, int wav, int nb, bool alt) {
+    if (f32) return wav ? fwd_fn_nb<float, 1>(nb, alt) : fwd_fn_nb<float, 0>(nb, alt);
+    return wav ? fwd_fn_nb<uint8_t, 1>(nb, alt) : fwd_fn_nb<uint8_t, 0>(nb, alt);
 }
 
 }  // namespace
 
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream) {
-    for (int b0 = 0; b0 < s.bands; b0 += kChunkBands) {
-        const int nb = s.bands - b0 < kChunkBands ? s.bands - b0 : kChunkBands;
-        void *fn = fwd_kernel_ptr(s.in_f32 != 0, s.wavelet, nb);
+    // Bands go in chunks of up to 8; the shifted-row instance (W % 4 == 2)
+    // holds more live registers per band and takes balanced chunks of <= 6.
+    const bool alt = s.alt != 0 && s.a4 == 0;
+    const int cap = alt ? kAltMaxBands : kChunkBands;
+    const int nchunks = (s.bands + cap - 1) / cap;
+    const int chunk = alt ? (s.bands + nchunks - 1) / nchunks : kChunkBands;
+    for (int b0 = 0; b0 < s.bands; b0 += chunk) {
+        const int nb = s.bands - b0 < chunk ? s.bands - b0 : chunk;
+        void *fn = fwd_kernel_ptr(s.in_f32 != 0, s.wavelet, nb, alt);
+        if (fn == nullptr) return cudaErrorInvalidValue;
         int occ = 0;
         cudaError_t e = resident_blocks(fn, kThreads, &occ);
         if (e != cudaSuccess) return e;

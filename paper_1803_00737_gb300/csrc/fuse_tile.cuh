@@ -119,6 +119,41 @@ __device__ __forceinline__ void store4(const OutPtrs &o, int64_t off, bool a4, b
     }
 }
 
+// Writes the 4 fused pixels (y, x..x+3) of one band on a row whose start is 2
+// pixels past a 16-byte boundary (W = 2 mod 4, odd rows): every lane but the
+// first writes the aligned vector (y, x-2..x+1), taking pixels x-2, x-1 from
+// its left neighbour; lane 0 writes (x, x+1) and the last lane of the strip
+// (x + 4 >= W or lane 31) also writes (x+2, x+3).  Every lane of the warp must
+// call it (warp shuffles); `active` masks the stores.
+__device__ __forceinline__ void store4_shifted(const OutPtrs &o, int64_t off, int lane, bool active,
+                                               bool two, bool last, const float *v) {
+    if (o.f32) {
+        const float p2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+        const float p3 = __shfl_up_sync(0xffffffffu, v[3], 1);
+        if (active) {
+            float *p = o.f32 + off;
+            if (lane > 0)
+                __stcs(reinterpret_cast<float4 *>(p - 2), make_float4(p2, p3, v[0], v[1]));
+            else
+                __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+            if (two && last) __stcs(reinterpret_cast<float2 *>(p + 2), make_float2(v[2], v[3]));
+        }
+    }
+    if (o.u8) {
+        const uint32_t q0 = f2u8(v[0]), q1 = f2u8(v[1]), q2 = f2u8(v[2]), q3 = f2u8(v[3]);
+        const uint32_t w = pack4(q0, q1, q2, q3);
+        const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+        if (active) {
+            uint8_t *p = o.u8 + off;
+            if (lane > 0)
+                __stcs(reinterpret_cast<unsigned int *>(p - 2), __byte_perm(pw, w, 0x5432u));
+            else
+                __stcs(reinterpret_cast<unsigned short *>(p), (unsigned short)(w & 0xffffu));
+            if (two && last) __stcs(reinterpret_cast<unsigned short *>(p + 2), (unsigned short)(w >> 16));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ scene
 
 // Everything a warp needs about one scene.  Band pointers are typed by the
@@ -134,7 +169,7 @@ struct SceneArgs {
     int32_t in_f32;    // inputs are float (else uint8)
     float gain;
     int32_t a4;        // W % 4 == 0 and PAN/outputs aligned for 4-pixel vectors
-    int32_t pad_;
+    int32_t alt;       // W % 4 == 2 with aligned planes: even rows aligned, odd rows 2 px past
 };
 
 // Column bookkeeping of one lane for one strip (sides are < 2^20, so 32 bits).
@@ -144,6 +179,7 @@ struct LaneCols {
     int32_t nA, nB, nC;  // MS columns n-1 (wrapped), n, n+1 (wrapped)
     bool active;         // x < W
     bool two;            // x + 2 < W (second MS column exists)
+    bool last;           // last active lane of the strip (x + 4 >= W or lane 31)
 };
 
 __device__ __forceinline__ int32_t wrap32(int32_t i, int32_t n) {
@@ -158,6 +194,7 @@ __device__ __forceinline__ LaneCols lane_cols(int64_t x0, int lane, int64_t W64)
     if (!c.active) x = 0;
     c.x = x;
     c.two = x + 2 < W;
+    c.last = lane == 31 || x + 4 >= W;
     c.cm = wrap32(x - 2, W);
     c.c2 = wrap32(x + 2, W);
     c.c4 = wrap32(x + 4, W);
@@ -204,16 +241,20 @@ __device__ __forceinline__ void d4_rowpass(const float *v, float *r) {
 
 // Haar: MS rows [m_s, m_e) of the strip starting at PAN column x0, bands
 // [b0, b0 + NB) (nb of them live).
-template <typename T, int NB>
+template <typename T, int NB, bool ALT>
 __device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
                                           int b0, int nb, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0;
+    const bool alt = ALT && !a4 && s.alt != 0;  // even rows aligned, odd rows 2 pixels past
+    // Vector path on even rows; the last lane (x = W-2) keeps the wrapped pair loads
+    // and 2-pixel stores there.
+    const bool a4e = a4 || (alt && c.two);
     const T *pan = static_cast<const T *>(s.pan);
     for (int64_t m = m_s; m < m_e; ++m) {
         float p0[4], p1[4];
-        load_row4(pan + (2 * m) * W, c, a4, p0);
+        load_row4(pan + (2 * m) * W, c, a4e, p0);
         load_row4(pan + (2 * m + 1) * W, c, a4, p1);
         float mv[NB][2];
 #pragma unroll
@@ -224,7 +265,7 @@ __device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_
                 mv[b][1] = ld1(ms + c.nC);
             }
         }
-        if (!c.active) continue;
+        if (!alt && !c.active) continue;
         // Eq. 1 along the rows, then along the columns: LL = 2x2 mean (exact in FP32 for 8-bit input).
         const float ll0 = ((p0[0] + p0[1]) * 0.5f + (p1[0] + p1[1]) * 0.5f) * 0.5f;
         const float ll1 = ((p0[2] + p0[3]) * 0.5f + (p1[2] + p1[3]) * 0.5f) * 0.5f;
@@ -237,21 +278,33 @@ __device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_
                 OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
                           s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
                 float v[4] = {p0[0] + e0, p0[1] + e0, p0[2] + e1, p0[3] + e1};
-                store4(o, (2 * m) * W + c.x, a4, c.two, v);
                 float w[4] = {p1[0] + e0, p1[1] + e0, p1[2] + e1, p1[3] + e1};
-                store4(o, (2 * m + 1) * W + c.x, a4, c.two, w);
+                if constexpr (ALT) {
+                    if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v);
+                    if (alt)
+                        store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, w);
+                    else if (c.active)
+                        store4(o, (2 * m + 1) * W + c.x, a4, c.two, w);
+                } else {
+                    store4(o, (2 * m) * W + c.x, a4, c.two, v);
+                    store4(o, (2 * m + 1) * W + c.x, a4, c.two, w);
+                }
             }
         }
     }
 }
 
 // D4: MS rows [m_s, m_e) of the strip starting at PAN column x0.
-template <typename T, int NB>
+template <typename T, int NB, bool ALT>
 __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
                                         int b0, int nb, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0;
+    const bool alt = ALT && !a4 && s.alt != 0;  // even rows aligned, odd rows 2 pixels past
+    // Vector path on even rows; the last lane (x = W-2) keeps the wrapped pair loads
+    // and 2-pixel stores there.
+    const bool a4e = a4 || (alt && c.two);
     const T *pan = static_cast<const T *>(s.pan);
     const float gain = s.gain;
 
@@ -261,11 +314,11 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
     float pc[4], pd[4];  // own PAN pixels of rows 2m, 2m+1 for the current m
     {
         float v[8];
-        load_row8(pan + (2 * mp) * W, c, a4, v);
+        load_row8(pan + (2 * mp) * W, c, a4e, v);
         d4_rowpass(v, r0);
         load_row8(pan + (2 * mp + 1) * W, c, a4, v);
         d4_rowpass(v, r1);
-        load_row8(pan + wrap(2 * mp + 2, H) * W, c, a4, v);
+        load_row8(pan + wrap(2 * mp + 2, H) * W, c, a4e, v);
         d4_rowpass(v, r2);
         pc[0] = v[2]; pc[1] = v[3]; pc[2] = v[4]; pc[3] = v[5];
         load_row8(pan + wrap(2 * mp + 3, H) * W, c, a4, v);
@@ -300,7 +353,7 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
         // Loads first (PAN rows 2m+2, 2m+3 and every band's MS row m), so their
         // latencies overlap.
         float va[8], vb[8];
-        load_row8(pan + wrap(2 * m + 2, H) * W, c, a4, va);
+        load_row8(pan + wrap(2 * m + 2, H) * W, c, a4e, va);
         load_row8(pan + wrap(2 * m + 3, H) * W, c, a4, vb);
         float mv[NB][3];
 #pragma unroll
@@ -338,7 +391,15 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
                     v1[q] = fmaf(kH3, hprev[b][q], fmaf(kH1, hc[q], pd[q]));
                     hprev[b][q] = hc[q];
                 }
-                if (c.active) {
+                if constexpr (ALT) {
+                    OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
+                              s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
+                    if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v0);
+                    if (alt)
+                        store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, v1);
+                    else if (c.active)
+                        store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+                } else if (c.active) {
                     OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
                               s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
                     store4(o, (2 * m) * W + c.x, a4, c.two, v0);
@@ -367,8 +428,10 @@ __host__ __device__ inline ItemGrid item_grid(int64_t H, int64_t W, int R) {
 }
 
 // Runs work item `item` of a scene: WAV < 0 selects the wavelet at run time
-// (batched kernel), 0 / 1 fixes Haar / D4 at compile time.
-template <typename T, int WAV, int NB>
+// (batched kernel), 0 / 1 fixes Haar / D4 at compile time.  ALT compiles the
+// shifted-row store path of widths W % 4 == 2 (taken when s.alt is set);
+// without it such scenes use the scalar edge path.
+template <typename T, int WAV, int NB, bool ALT = false>
 __device__ __forceinline__ void run_item(const SceneArgs &s, int64_t item, int64_t strips_x, int R,
                                          int b0, int nb, int lane) {
     const int64_t sx = item % strips_x, sy = item / strips_x;
@@ -376,9 +439,9 @@ __device__ __forceinline__ void run_item(const SceneArgs &s, int64_t item, int64
     const int64_t m_s = sy * R;
     const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
     if (WAV == 0 || (WAV < 0 && s.wavelet == 0))
-        haar_item<T, NB>(s, x0, m_s, m_e, b0, nb, lane);
+        haar_item<T, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
     else
-        d4_item<T, NB>(s, x0, m_s, m_e, b0, nb, lane);
+        d4_item<T, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
 }
 
 }  // namespace dwtfuse
