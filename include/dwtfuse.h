@@ -177,6 +177,23 @@ int dwtfuse_qnr(const void *fused, int fused_dtype, const void *const *ms, const
                 size_t ws_bytes, double *out_qnr, double *out_dlambda, double *out_ds,
                 void *stream);
 
+/*
+ * Fused forward followed by the metrics of its uint8 product, in one call:
+ * the same outputs as dwtfuse_fuse(pan, ms, ..., out_f32, out_u8) and then
+ * dwtfuse_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, ...) into
+ * out_device (ERGAS, QNR, D_lambda, D_s as four device doubles).  With uint8
+ * inputs and up to 6 bands the forward scores its product on chip (the
+ * PAN-resolution half of the metrics needs no read of the fused bands, PAN or
+ * MS); otherwise the two calls run one after the other.  Arguments and errors
+ * are those of the two calls; out_u8 is required, out_f32 optional; the
+ * workspace is the metrics workspace.  Asynchronous on `stream`, capturable
+ * in a CUDA graph.  The ERGAS value equals the separate calls' exactly; Q
+ * sums are accumulated in another order (agreement to ~1e-6).
+ */
+int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                         int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
+                         size_t ws_bytes, double *out_device, void *stream);
+
 /* One scene of a batched call (all pointers on the device, as above). */
 typedef struct {
     const void *pan;

@@ -70,6 +70,8 @@ _SIGS = {
     "dwtfuse_metrics_workspace_size": (_sz, []),
     "dwtfuse_metrics": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
                              _vp, _vp]),
+    "dwtfuse_fuse_metrics": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp, _sz,
+                                  _vp, _vp]),
     "dwtfuse_ergas": (_i, [_vp, _i, ctypes.POINTER(_vp), _i, _i, _i64, _i64, _vp, _sz,
                            ctypes.POINTER(ctypes.c_double), _vp]),
     "dwtfuse_qnr": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
@@ -274,6 +276,31 @@ def dwtfuse_metrics(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch
                                _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
                                _dev(out_device, "out_device"), _stream(stream))
     _check(st, "dwtfuse_metrics")
+
+
+def dwtfuse_fuse_metrics(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
+                         out_u8: torch.Tensor, workspace: torch.Tensor, out_device: torch.Tensor,
+                         stream=None) -> None:
+    """Fused forward into the caller's outputs, then ERGAS, QNR, D_lambda, D_s
+    of the uint8 product into out_device[0:4] (async; see dwtfuse.h)."""
+    bands = _bands(ms)
+    H, W = pan.shape
+    ptrs = (_vp * len(bands))(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
+    for b, m in enumerate(bands):
+        if m.dtype != pan.dtype or tuple(m.shape) != (H // 2, W // 2):
+            raise ValueError(f"ms[{b}] must be {pan.dtype} of shape ({H // 2}, {W // 2})")
+    for name, o, dt in (("out_f32", out_f32, torch.float32), ("out_u8", out_u8, torch.uint8)):
+        if o is not None and (o.dtype != dt or tuple(o.shape) != (len(bands), H, W)):
+            raise ValueError(f"{name} must be {dt} of shape ({len(bands)}, {H}, {W})")
+    if out_device.dtype != torch.float64 or out_device.numel() < 4:
+        raise ValueError("out_device must be a float64 CUDA tensor with >= 4 elements")
+    st = lib().dwtfuse_fuse_metrics(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet),
+                                    _dtype_code(pan, "pan"),
+                                    _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                                    _dev(out_u8, "out_u8"), _dev(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(),
+                                    _dev(out_device, "out_device"), _stream(stream))
+    _check(st, "dwtfuse_fuse_metrics")
 
 
 def dwtfuse_ergas(fused: torch.Tensor, ms, workspace: torch.Tensor, stream=None) -> float:

@@ -278,6 +278,33 @@ int dwtfuse_metrics(const void *fused, int fused_dtype, const void *const *ms, c
     return cuda_status(launch_metrics(m, static_cast<cudaStream_t>(stream)));
 }
 
+int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                         int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
+                         size_t ws_bytes, double *out_device, void *stream) {
+    if (!out_u8 || !out_device) return DWTFUSE_EINVAL;
+    if (!aligned(out_device, 8)) return DWTFUSE_EALIGN;
+    SceneArgs s;
+    int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
+    if (st != DWTFUSE_OK) return st;
+    MetricLaunch m;
+    st = make_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, bands, H, W, kMetricWindow, true, workspace,
+                      ws_bytes, &m);
+    if (st != DWTFUSE_OK) return st;
+    m.result = out_device;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (fuse_metrics_supported(s)) {
+        int ctas = 0;
+        e = launch_fuse_metrics(s, m.workspace + kMetricPanPartialOffset, kMetricStride, &ctas, cs);
+        m.pan_done = 1;
+        m.pan_ctas = ctas;
+    } else {
+        e = launch_fuse(s, rows_per_item(), 0, cs);
+    }
+    if (e == cudaSuccess) e = launch_metrics(m, cs);
+    return cuda_status(e);
+}
+
 static int metrics_to_host(const MetricLaunch &m, void *stream, double *out4) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_metrics(m, s);

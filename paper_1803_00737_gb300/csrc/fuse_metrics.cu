@@ -1,0 +1,331 @@
+// Fused forward with the PAN-resolution half of the quality metrics in the
+// same kernel.  The forward (Sec. 2, Eq. 1-16) is the one of fuse_fwd.cu; the
+// metrics are those of metrics.cu (ERGAS squared errors against MS repeated
+// 2x2, window sums of Q(F_l, F_r) and Q(F_l, PAN) over 32 x 32 windows, the
+// paper's Sec. 4 / Table 3 scores).  Scoring the uint8 product while it is
+// still on chip saves the metric pass's read of every fused band, of PAN and
+// of MS (about a quarter of a benchmark step's HBM traffic).
+//
+// Work item: a warp strip of 128 PAN columns (four windows side by side, 8
+// lanes each) over R MS rows, R a multiple of 16 and items starting on window
+// rows.  Every two MS rows (4 PAN rows) the warp parks its uint8 pixels,
+// the matching PAN pixels and the MS reference values in a per-warp shared
+// tile (a private spill area: each lane reads back only its own words, so the
+// fusion's registers are free again) and adds their sums into per-lane
+// shared slots: signed-byte dp4a sums, exact in int32.  At the end of each
+// window row the 8 lanes of a window add up their slots, each computes Q for
+// up to 4 of the window's image pairs (integer numerators, FP32 ratio), and
+// the value goes to a per-warp float slot of that window position; squared
+// errors go to per-lane int64 slots.  The CTA writes one partial row in the
+// layout of the separate PAN-resolution pass, so the MS-resolution pass and
+// the finalize kernel of metrics.cu complete the figures unchanged.
+#include "fuse_tile.cuh"
+#include "launch.h"
+#include "metric_q.cuh"
+
+namespace dwtfuse {
+
+namespace {
+
+constexpr int kFmThreads = 256;
+constexpr int kFmWarps = kFmThreads / 32;
+constexpr int kFmWinMs = 16;  // MS rows per 32-row window row
+
+template <int NB>
+struct FmLayout {
+    static constexpr int K = NB + 1;                  // images: NB bands, then PAN
+    static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs (b < c), then band-PAN pairs
+    static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
+    // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
+    static constexpr int kTile = K * 4 * 32;          // uint8 words of 4 PAN rows: bands, PAN
+    static constexpr int kRep = NB * 2 * 32;          // MS reference words of 2 MS rows
+    static constexpr int kSums = NS * 32;
+    static constexpr int kQ = 4 * P;                  // float Q sums per window position
+    static constexpr int kWords = (kTile + kRep + kSums + kQ + 1) & ~1;
+    static constexpr int kWarpBytes = kWords * 4 + NB * 32 * 8;  // + int64 squared errors per lane
+    static constexpr int kSmem = kFmWarps * kWarpBytes;
+};
+
+// Bands b < c of band-band pair p (p < NB(NB-1)/2), in the order of the pair sums.
+template <int NB>
+__device__ __forceinline__ void pair_bands(int p, int &b, int &c) {
+    b = 0;
+    while (p >= NB - 1 - b) {
+        p -= NB - 1 - b;
+        ++b;
+    }
+    c = b + 1 + p;
+}
+
+template <int NB>
+struct MetricEmit {
+    using L = FmLayout<NB>;
+    static constexpr bool kAllLanes = true;
+    static constexpr int K = L::K, P = L::P, NS = L::NS;
+    const SceneArgs &s;
+    const LaneCols &c;
+    uint32_t *tile, *rep;
+    int *sums;
+    float *qs;
+    long long *se64;
+    int64_t x0, m_s, m_e;
+    int lane;
+    bool a4;
+    uint32_t keep;  // bytes of this lane's 4-pixel words inside the image
+
+    __device__ __forceinline__ void band(int b, int64_t m, const float *v0, const float *v1, float mn,
+                                         float mn1) const {
+        const uint32_t w0 = pack4(f2u8(v0[0]), f2u8(v0[1]), f2u8(v0[2]), f2u8(v0[3]));
+        const uint32_t w1 = pack4(f2u8(v1[0]), f2u8(v1[1]), f2u8(v1[2]), f2u8(v1[3]));
+        const int r = (int)((m - m_s) & 1);
+        tile[(b * 4 + 2 * r) * 32 + lane] = w0;
+        tile[(b * 4 + 2 * r + 1) * 32 + lane] = w1;
+        // ERGAS reference: MS(m, n), MS(m, n+1) each repeated over 2 PAN columns.
+        rep[(b * 2 + r) * 32 + lane] = __byte_perm(f2u8(mn), f2u8(mn1), 0x4400u);
+        if (!c.active) return;
+        const int64_t HW = s.H * s.W;
+        const int64_t o0 = (int64_t)b * HW + (2 * m) * s.W + c.x, o1 = o0 + s.W;
+        if (s.out_f32) {
+            float *p0 = s.out_f32 + o0, *p1 = s.out_f32 + o1;
+            if (a4) {
+                __stcs(reinterpret_cast<float4 *>(p0), make_float4(v0[0], v0[1], v0[2], v0[3]));
+                __stcs(reinterpret_cast<float4 *>(p1), make_float4(v1[0], v1[1], v1[2], v1[3]));
+            } else {
+                __stcs(reinterpret_cast<float2 *>(p0), make_float2(v0[0], v0[1]));
+                __stcs(reinterpret_cast<float2 *>(p1), make_float2(v1[0], v1[1]));
+                if (c.two) {
+                    __stcs(reinterpret_cast<float2 *>(p0 + 2), make_float2(v0[2], v0[3]));
+                    __stcs(reinterpret_cast<float2 *>(p1 + 2), make_float2(v1[2], v1[3]));
+                }
+            }
+        }
+        uint8_t *q0 = s.out_u8 + o0, *q1 = s.out_u8 + o1;
+        if (a4) {
+            __stcs(reinterpret_cast<unsigned int *>(q0), w0);
+            __stcs(reinterpret_cast<unsigned int *>(q1), w1);
+        } else {
+            __stcs(reinterpret_cast<unsigned short *>(q0), (unsigned short)(w0 & 0xffffu));
+            __stcs(reinterpret_cast<unsigned short *>(q1), (unsigned short)(w1 & 0xffffu));
+            if (c.two) {
+                __stcs(reinterpret_cast<unsigned short *>(q0 + 2), (unsigned short)(w0 >> 16));
+                __stcs(reinterpret_cast<unsigned short *>(q1 + 2), (unsigned short)(w1 >> 16));
+            }
+        }
+    }
+
+    // Sums of the tile's first `nr` PAN rows into this lane's slots.  qon: the
+    // lane's window is inside the image (window sums wanted).
+    __device__ __forceinline__ void score(int nr, bool qon) const {
+        int s1[K], s2[K], sxy[P], se[NB];
+#pragma unroll
+        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) sxy[k] = 0;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se[b] = 0;
+        for (int r = 0; r < nr; ++r) {
+            uint32_t f[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) f[k] = tile[(k * 4 + r) * 32 + lane];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const uint32_t d = __vabsdiffu4(f[b], rep[(b * 2 + (r >> 1)) * 32 + lane]) & keep;
+                se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
+            }
+            if (qon) {
+                int v[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    v[k] = (int)(f[k] ^ 0x80808080u);  // signed bytes X - 128
+                    s1[k] = __dp4a(v[k], 0x01010101, s1[k]);
+                    s2[k] = __dp4a(v[k], v[k], s2[k]);
+                }
+                int idx = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int c2 = b + 1; c2 < NB; ++c2, ++idx) sxy[idx] = __dp4a(v[b], v[c2], sxy[idx]);
+#pragma unroll
+                for (int b = 0; b < NB; ++b, ++idx) sxy[idx] = __dp4a(v[b], v[NB], sxy[idx]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) se64[b * 32 + lane] += se[b];
+        if (qon) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                sums[k * 32 + lane] += s1[k];
+                sums[(K + k) * 32 + lane] += s2[k];
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k) sums[(2 * K + k) * 32 + lane] += sxy[k];
+        }
+    }
+
+    // End of a window row: the 8 lanes of each window add up their slots
+    // (slot of the group's first lane), then lane j of the group computes Q
+    // for pairs j, j+8, ...  `full` (warp-uniform): the window row lies inside
+    // the image.  Every lane's slots are cleared.
+    __device__ __forceinline__ void flush(bool full) const {
+        const int g = lane >> 3, j = lane & 7, g0 = 8 * g;
+        if (full) {
+            __syncwarp();
+            for (int k = j; k < NS; k += 8) {
+                int t = 0;
+#pragma unroll
+                for (int l = 0; l < 8; ++l) t += sums[k * 32 + g0 + l];
+                sums[k * 32 + g0] = t;
+            }
+            __syncwarp();
+            if (x0 + 32 * (g + 1) <= s.W) {
+                for (int p = j; p < P; p += 8) {
+                    int b, c2;
+                    if (p < P - NB) {
+                        pair_bands<NB>(p, b, c2);
+                    } else {
+                        b = p - (P - NB);
+                        c2 = NB;
+                    }
+                    const float q = q_exact(sums[b * 32 + g0], sums[(K + b) * 32 + g0], sums[c2 * 32 + g0],
+                                            sums[(K + c2) * 32 + g0], sums[(2 * K + p) * 32 + g0], 1);
+                    qs[g * P + p] += q;
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) sums[k * 32 + lane] = 0;
+    }
+
+    __device__ __forceinline__ void row_end(int64_t m, const float *pan0, const float *pan1) const {
+        const int r = (int)((m - m_s) & 1);
+        tile[(NB * 4 + 2 * r) * 32 + lane] = pack4(f2u8(pan0[0]), f2u8(pan0[1]), f2u8(pan0[2]), f2u8(pan0[3]));
+        tile[(NB * 4 + 2 * r + 1) * 32 + lane] = pack4(f2u8(pan1[0]), f2u8(pan1[1]), f2u8(pan1[2]), f2u8(pan1[3]));
+        const bool last = m + 1 == m_e;
+        if (r == 0 && !last) return;
+        // Rows 2m' .. 2m+1 of the window row starting at PAN row y_win.
+        const int64_t y_win = ((2 * m) / 32) * 32;
+        const bool row_full = y_win + 32 <= s.H;
+        const bool qon = row_full && x0 + 32 * ((lane >> 3) + 1) <= s.W;
+        score(2 * (r + 1), qon);
+        if ((m - m_s + 1) % kFmWinMs == 0 || last) flush(row_full);
+    }
+};
+
+template <typename T, int WAV, int NB>
+__global__ void __launch_bounds__(kFmThreads, 2)
+fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int stride, int64_t strips_x,
+                    int64_t items, int R) {
+    using L = FmLayout<NB>;
+    extern __shared__ __align__(16) unsigned char fm_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *wb = fm_smem + warp * L::kWarpBytes;
+    uint32_t *tile = reinterpret_cast<uint32_t *>(wb);
+    uint32_t *rep = tile + L::kTile;
+    int *sums = reinterpret_cast<int *>(rep + L::kRep);
+    float *qs = reinterpret_cast<float *>(sums + L::kSums);
+    long long *se64 = reinterpret_cast<long long *>(wb + L::kWords * 4);
+    for (int k = 0; k < L::NS; ++k) sums[k * 32 + lane] = 0;
+    for (int k = lane; k < L::kQ; k += 32) qs[k] = 0.f;
+    for (int b = 0; b < NB; ++b) se64[b * 32 + lane] = 0;
+    __syncwarp();
+
+    const int64_t nwarps = (int64_t)gridDim.x * kFmWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kFmWarps + warp; it < items; it += nwarps) {
+        const int64_t sx = it % strips_x, sy = it / strips_x;
+        const int64_t x0 = sx * kWarpCols;
+        const int64_t m_s = sy * R;
+        const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
+        const LaneCols c = lane_cols(x0, lane, s.W);
+        const int64_t x = x0 + 4 * lane;
+        const uint32_t keep = x + 4 <= s.W ? 0xffffffffu : (x + 2 <= s.W ? 0x0000ffffu : 0u);
+        const bool a4 = s.a4 != 0;
+        MetricEmit<NB> out{s, c, tile, rep, sums, qs, se64, x0, m_s, m_e, lane, a4, keep};
+        if (WAV == 0)
+            haar_rows<T, NB>(s, c, a4, a4, m_s, m_e, 0, NB, out);
+        else
+            d4_rows<T, NB>(s, c, a4, a4, m_s, m_e, 0, NB, out);
+    }
+
+    // One partial row per CTA, in the layout of the PAN-resolution pass:
+    // Q sums of the P pairs, then the NB squared-error sums (fixed order).
+    __syncthreads();
+    double *outp = partial + (int64_t)blockIdx.x * stride;
+    for (int k = threadIdx.x; k < L::P + NB; k += kFmThreads) {
+        double acc = 0.0;
+        for (int w = 0; w < kFmWarps; ++w) {
+            const unsigned char *wbw = fm_smem + w * L::kWarpBytes;
+            if (k < L::P) {
+                const float *qw = reinterpret_cast<const float *>(wbw) + L::kTile + L::kRep + L::kSums;
+                for (int g = 0; g < 4; ++g) acc += (double)qw[g * L::P + k];
+            } else {
+                const long long *sw = reinterpret_cast<const long long *>(wbw + L::kWords * 4);
+                long long t = 0;
+                for (int l = 0; l < 32; ++l) t += sw[(k - L::P) * 32 + l];
+                acc += (double)t;
+            }
+        }
+        outp[k] = acc;
+    }
+}
+
+template <int WAV, int NB>
+void *fm_fn() { return reinterpret_cast<void *>(&fuse_metrics_kernel<uint8_t, WAV, NB>); }
+
+void *fm_kernel_ptr(int wav, int nb, int *smem) {
+    switch (nb) {
+#define DWTFUSE_FM(NBV)                        \
+    case NBV:                                  \
+        *smem = FmLayout<NBV>::kSmem;          \
+        return wav ? fm_fn<1, NBV>() : fm_fn<0, NBV>();
+        DWTFUSE_FM(1) DWTFUSE_FM(2) DWTFUSE_FM(3) DWTFUSE_FM(4) DWTFUSE_FM(5) DWTFUSE_FM(6)
+#undef DWTFUSE_FM
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+bool fuse_metrics_supported(const SceneArgs &s) {
+    return !s.in_f32 && s.out_u8 != nullptr && s.bands >= 1 && s.bands <= kFuseMetricsMaxBands;
+}
+
+cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas,
+                                cudaStream_t stream) {
+    int smem = 0;
+    void *fn = fm_kernel_ptr(s.wavelet, s.bands, &smem);
+    if (fn == nullptr || s.in_f32 || s.out_u8 == nullptr) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFmThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = (int64_t)sms * occ;
+    // Rows per item: a multiple of the 16 MS rows of a window row, balancing the last wave.
+    int R = kFmWinMs;
+    double best = 1e300;
+    for (int r = kFmWinMs; r <= 4 * kFmWinMs; r += kFmWinMs) {
+        const ItemGrid g = item_grid(s.H, s.W, r);
+        const double cost = (double)((g.items + cap * kFmWarps - 1) / (cap * kFmWarps)) * (r + 1);
+        if (cost <= best) {
+            best = cost;
+            R = r;
+        }
+    }
+    const ItemGrid g = item_grid(s.H, s.W, R);
+    int64_t grid = (g.items + kFmWarps - 1) / kFmWarps;
+    if (grid > cap) grid = cap;
+    if (grid > kMetricMaxCtas) grid = kMetricMaxCtas;
+    if (grid < 1) grid = 1;
+    *ctas = (int)grid;
+    SceneArgs sa = s;
+    int64_t strips_x = g.strips_x, items = g.items;
+    int strd = stride, Rv = R;
+    void *args[] = {&sa, &pan_partial, &strd, &strips_x, &items, &Rv};
+    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kFmThreads), args, (size_t)smem, stream);
+}
+
+}  // namespace dwtfuse

@@ -237,25 +237,27 @@ __device__ __forceinline__ void d4_rowpass(const float *v, float *r) {
     r[2] = fmaf(kH3, v[7], fmaf(kH2, v[6], fmaf(kH1, v[5], kH0 * v[4])));
 }
 
-// ------------------------------------------------------------------ one work item
+// ------------------------------------------------------------------ row walkers
+//
+// A walker takes one lane's columns (LaneCols) down MS rows [m_s, m_e) and
+// hands every band's two fused PAN rows 2m, 2m+1 (4 pixels per lane) to an
+// emitter: out.band(b, m, v0, v1, mn, mn1) per band, with the band's MS values
+// at MS columns n = x/2 and n+1 (the ones the lane's pixels were made from),
+// then out.row_end(m, pan0, pan1) once per MS row with the lane's PAN pixels
+// of rows 2m and 2m+1.  Emit::kAllLanes: the emitter needs every lane (warp
+// shuffles), so idle lanes compute on column 0 and call it too.  ld_even /
+// ld_odd select the 4-pixel PAN loads on even / odd rows.
 
-// Haar: MS rows [m_s, m_e) of the strip starting at PAN column x0, bands
-// [b0, b0 + NB) (nb of them live).
-template <typename T, int NB, bool ALT>
-__device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
-                                          int b0, int nb, int lane) {
-    const int64_t W = s.W, H = s.H, W2 = W >> 1, HW = H * W;
-    const LaneCols c = lane_cols(x0, lane, W);
-    const bool a4 = s.a4 != 0;
-    const bool alt = ALT && !a4 && s.alt != 0;  // even rows aligned, odd rows 2 pixels past
-    // Vector path on even rows; the last lane (x = W-2) keeps the wrapped pair loads
-    // and 2-pixel stores there.
-    const bool a4e = a4 || (alt && c.two);
+// Haar (Eq. 1-2, 11-12).
+template <typename T, int NB, class Emit>
+__device__ __forceinline__ void haar_rows(const SceneArgs &s, const LaneCols &c, bool ld_even, bool ld_odd,
+                                          int64_t m_s, int64_t m_e, int b0, int nb, Emit &out) {
+    const int64_t W = s.W, W2 = W >> 1;
     const T *pan = static_cast<const T *>(s.pan);
     for (int64_t m = m_s; m < m_e; ++m) {
         float p0[4], p1[4];
-        load_row4(pan + (2 * m) * W, c, a4e, p0);
-        load_row4(pan + (2 * m + 1) * W, c, a4, p1);
+        load_row4(pan + (2 * m) * W, c, ld_even, p0);
+        load_row4(pan + (2 * m + 1) * W, c, ld_odd, p1);
         float mv[NB][2];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -265,7 +267,7 @@ __device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_
                 mv[b][1] = ld1(ms + c.nC);
             }
         }
-        if (!alt && !c.active) continue;
+        if (!Emit::kAllLanes && !c.active) continue;
         // Eq. 1 along the rows, then along the columns: LL = 2x2 mean (exact in FP32 for 8-bit input).
         const float ll0 = ((p0[0] + p0[1]) * 0.5f + (p1[0] + p1[1]) * 0.5f) * 0.5f;
         const float ll1 = ((p0[2] + p0[3]) * 0.5f + (p1[2] + p1[3]) * 0.5f) * 0.5f;
@@ -275,36 +277,20 @@ __device__ __forceinline__ void haar_item(const SceneArgs &s, int64_t x0, int64_
                 // Eq. 11-12 on an LL-only image repeat each coefficient over its 2x2 block.
                 const float e0 = fmaf(s.gain, mv[b][0], -ll0);
                 const float e1 = fmaf(s.gain, mv[b][1], -ll1);
-                OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
-                          s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
                 float v[4] = {p0[0] + e0, p0[1] + e0, p0[2] + e1, p0[3] + e1};
                 float w[4] = {p1[0] + e0, p1[1] + e0, p1[2] + e1, p1[3] + e1};
-                if constexpr (ALT) {
-                    if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v);
-                    if (alt)
-                        store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, w);
-                    else if (c.active)
-                        store4(o, (2 * m + 1) * W + c.x, a4, c.two, w);
-                } else {
-                    store4(o, (2 * m) * W + c.x, a4, c.two, v);
-                    store4(o, (2 * m + 1) * W + c.x, a4, c.two, w);
-                }
+                out.band(b, m, v, w, mv[b][0], mv[b][1]);
             }
         }
+        out.row_end(m, p0, p1);
     }
 }
 
-// D4: MS rows [m_s, m_e) of the strip starting at PAN column x0.
-template <typename T, int NB, bool ALT>
-__device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
-                                        int b0, int nb, int lane) {
-    const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
-    const LaneCols c = lane_cols(x0, lane, W);
-    const bool a4 = s.a4 != 0;
-    const bool alt = ALT && !a4 && s.alt != 0;  // even rows aligned, odd rows 2 pixels past
-    // Vector path on even rows; the last lane (x = W-2) keeps the wrapped pair loads
-    // and 2-pixel stores there.
-    const bool a4e = a4 || (alt && c.two);
+// D4 (Eq. 3-10, 13-16).
+template <typename T, int NB, class Emit>
+__device__ __forceinline__ void d4_rows(const SceneArgs &s, const LaneCols &c, bool ld_even, bool ld_odd,
+                                        int64_t m_s, int64_t m_e, int b0, int nb, Emit &out) {
+    const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1;
     const T *pan = static_cast<const T *>(s.pan);
     const float gain = s.gain;
 
@@ -314,14 +300,14 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
     float pc[4], pd[4];  // own PAN pixels of rows 2m, 2m+1 for the current m
     {
         float v[8];
-        load_row8(pan + (2 * mp) * W, c, a4e, v);
+        load_row8(pan + (2 * mp) * W, c, ld_even, v);
         d4_rowpass(v, r0);
-        load_row8(pan + (2 * mp + 1) * W, c, a4, v);
+        load_row8(pan + (2 * mp + 1) * W, c, ld_odd, v);
         d4_rowpass(v, r1);
-        load_row8(pan + wrap(2 * mp + 2, H) * W, c, a4e, v);
+        load_row8(pan + wrap(2 * mp + 2, H) * W, c, ld_even, v);
         d4_rowpass(v, r2);
         pc[0] = v[2]; pc[1] = v[3]; pc[2] = v[4]; pc[3] = v[5];
-        load_row8(pan + wrap(2 * mp + 3, H) * W, c, a4, v);
+        load_row8(pan + wrap(2 * mp + 3, H) * W, c, ld_odd, v);
         d4_rowpass(v, r3);
         pd[0] = v[2]; pd[1] = v[3]; pd[2] = v[4]; pd[3] = v[5];
     }
@@ -353,8 +339,8 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
         // Loads first (PAN rows 2m+2, 2m+3 and every band's MS row m), so their
         // latencies overlap.
         float va[8], vb[8];
-        load_row8(pan + wrap(2 * m + 2, H) * W, c, a4e, va);
-        load_row8(pan + wrap(2 * m + 3, H) * W, c, a4, vb);
+        load_row8(pan + wrap(2 * m + 2, H) * W, c, ld_even, va);
+        load_row8(pan + wrap(2 * m + 3, H) * W, c, ld_odd, vb);
         float mv[NB][3];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -391,27 +377,65 @@ __device__ __forceinline__ void d4_item(const SceneArgs &s, int64_t x0, int64_t 
                     v1[q] = fmaf(kH3, hprev[b][q], fmaf(kH1, hc[q], pd[q]));
                     hprev[b][q] = hc[q];
                 }
-                if constexpr (ALT) {
-                    OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
-                              s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
-                    if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v0);
-                    if (alt)
-                        store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, v1);
-                    else if (c.active)
-                        store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
-                } else if (c.active) {
-                    OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
-                              s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
-                    store4(o, (2 * m) * W + c.x, a4, c.two, v0);
-                    store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
-                }
+                out.band(b, m, v0, v1, mv[b][1], mv[b][2]);
             }
         }
+        out.row_end(m, pc, pd);
 #pragma unroll
         for (int k = 0; k < 3; ++k) { r0[k] = r2[k]; r1[k] = r3[k]; }
         pc[0] = va[2]; pc[1] = va[3]; pc[2] = va[4]; pc[3] = va[5];
         pd[0] = vb[2]; pd[1] = vb[3]; pd[2] = vb[4]; pd[3] = vb[5];
     }
+}
+
+// ------------------------------------------------------------------ direct emitter
+
+// Every lane writes its own 4 pixels to global memory.  ALT: the W % 4 == 2
+// instance (even rows vectorised, odd rows through store4_shifted).
+template <bool ALT>
+struct DirectEmit {
+    static constexpr bool kAllLanes = ALT;
+    const SceneArgs &s;
+    const LaneCols &c;
+    int b0, lane;
+    bool a4, a4e, alt;
+
+    __device__ __forceinline__ void band(int b, int64_t m, const float *v0, const float *v1, float, float) const {
+        const int64_t W = s.W, HW = s.H * s.W;
+        if constexpr (ALT) {
+            OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
+                      s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
+            if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v0);
+            if (alt)
+                store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, v1);
+            else if (c.active)
+                store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+        } else if (c.active) {
+            OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
+                      s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
+            store4(o, (2 * m) * W + c.x, a4, c.two, v0);
+            store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+        }
+    }
+    __device__ __forceinline__ void row_end(int64_t, const float *, const float *) const {}
+};
+
+// One warp strip: 128 PAN columns from x0, MS rows [m_s, m_e), bands
+// [b0, b0 + NB) (nb of them live), written directly.
+template <typename T, int WAV, int NB, bool ALT>
+__device__ __forceinline__ void direct_item(const SceneArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
+                                            int b0, int nb, int lane) {
+    const LaneCols c = lane_cols(x0, lane, s.W);
+    const bool a4 = s.a4 != 0;
+    const bool alt = ALT && !a4 && s.alt != 0;  // even rows aligned, odd rows 2 pixels past
+    // Vector path on even rows; the last lane (x = W-2) keeps the wrapped pair loads
+    // and 2-pixel stores there.
+    const bool a4e = a4 || (alt && c.two);
+    DirectEmit<ALT> out{s, c, b0, lane, a4, a4e, alt};
+    if (WAV == 0)
+        haar_rows<T, NB>(s, c, a4e, a4, m_s, m_e, b0, nb, out);
+    else
+        d4_rows<T, NB>(s, c, a4e, a4, m_s, m_e, b0, nb, out);
 }
 
 // Geometry of a scene's work items: strips of 128 PAN columns times runs of R MS rows.
@@ -439,9 +463,9 @@ __device__ __forceinline__ void run_item(const SceneArgs &s, int64_t item, int64
     const int64_t m_s = sy * R;
     const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
     if (WAV == 0 || (WAV < 0 && s.wavelet == 0))
-        haar_item<T, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
+        direct_item<T, 0, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
     else
-        d4_item<T, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
+        direct_item<T, 1, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
 }
 
 }  // namespace dwtfuse

@@ -47,7 +47,13 @@ struct MetricLaunch {
     int32_t a32_ms;     // uint8 MS-pass fast path: W % 32 == 0, PAN and MS 16-byte aligned
     double *workspace;  // kMetricWorkspaceBytes, 8-byte aligned
     double *result;     // device pointer for the 4 results, or nullptr
+    int32_t pan_done;   // PAN-resolution partial rows already written (fused forward + metrics)
+    int32_t pan_ctas;   // ... and how many
 };
+
+// Fused forward + PAN-resolution metrics (fuse_metrics.cu): uint8 inputs, a
+// uint8 output, up to this many bands in one launch.
+constexpr int kFuseMetricsMaxBands = 6;
 
 // MS rows per work item that balance the last wave of a grid of `warps`
 // warps: minimises ceil(items / warps) * (R + 1) over R in [16, 64] (the +1
@@ -91,6 +97,12 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
                                  float *gpan, float *const *gms, int R, cudaStream_t stream);
 cudaError_t launch_dwt2(const DwtLaunch &d, cudaStream_t stream);
 cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream);
+bool fuse_metrics_supported(const SceneArgs &s);
+// Writes the PAN-resolution partial rows (stride doubles apart) and their count.
+cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas,
+                                cudaStream_t stream);
+// Offset of the PAN-resolution partial rows in the metrics workspace (doubles).
+constexpr int64_t kMetricPanPartialOffset = 8;
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);
 

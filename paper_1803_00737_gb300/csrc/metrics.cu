@@ -30,6 +30,7 @@
 
 #include "fuse_tile.cuh"
 #include "launch.h"
+#include "metric_q.cuh"
 
 namespace dwtfuse {
 
@@ -99,27 +100,6 @@ __device__ __forceinline__ int xor_sum8(int v) {
 struct WinSums {
     double sx, sxx, sy, syy, sxy;
 };
-
-// Q of one window, given exact integer sums (8-bit data).  ys = scale of y.
-__device__ __forceinline__ float q_exact(long long sx, long long sxx, long long sy, long long syy,
-                                         long long sxy, int ys) {
-    const long long n = kN;
-    const long long vx = n * sxx - sx * sx;                 // n^2 var(x)
-    const long long vy = n * syy - sy * sy;                 // ys^2 n^2 var(y)
-    const long long cxy = n * sxy - sx * sy;                // ys n^2 cov(x, y)
-    const long long ax = sx + 128 * n;                      // n mean(X)
-    const long long ay = sy + 128 * n * ys;                 // ys n mean(Y)
-    const float inv = 1.0f / (float)ys, inv2 = inv * inv;
-    const float fvx = (float)vx, fvy = (float)vy * inv2, fc = (float)cxy * inv;
-    const float fax = (float)ax, fay = (float)ay * inv;
-    const float den = (fvx + fvy) * (fax * fax + fay * fay);
-    if (vx + vy == 0 || (ax == 0 && ay == 0)) {
-        // zero denominator: identical windows <=> sum (ys x - y)^2 = 0
-        const long long d2 = (long long)ys * ys * sxx - 2LL * ys * sxy + syy;
-        return (d2 == 0) ? 1.0f : 0.0f;
-    }
-    return 4.0f * fc * fax * fay / den;
-}
 
 // Q of one window from float sums (float data): numerators in FP64.
 __device__ __forceinline__ float q_float(float sx, float sxx, float sy, float syy, float sxy) {
@@ -904,8 +884,11 @@ metrics_ms_kernel(const __grid_constant__ MetricArgs a) {
 // D_lambda, D_s (QNR terms NaN when not requested or when no full window
 // exists at either resolution).  Each warp reduces one column of partials:
 // lanes stride over the CTAs, then a xor butterfly (a fixed order, so the
-// result is the same on every run).
-__global__ void __launch_bounds__(256)
+// result is the same on every run).  The lane loop is unrolled so that its
+// loads are in flight together: the partials sit in L2 and each round trip
+// is a few hundred cycles.
+constexpr int kFinalizeThreads = 1024;
+__global__ void __launch_bounds__(kFinalizeThreads)
 metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, int ctas_ms,
                         int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
                         int64_t nwin_ms, double *out) {
@@ -919,6 +902,7 @@ metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_
         const double *part = ms ? ms_part : pan_part;
         const int ctas = ms ? ctas_ms : ctas_pan;
         double a = 0.0;
+#pragma unroll 8
         for (int c = lane; c < ctas; c += 32) a += part[(int64_t)c * stride + kk];
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (lane == 0) (ms ? tot_ms : tot_pan)[kk] = a;
@@ -1064,12 +1048,15 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     a.stride = kMetricStride;
     const bool fast = !m.fused_f32 && !m.in_f32;
     double *out = m.workspace;
-    double *pan_part = m.workspace + 8;
+    double *pan_part = m.workspace + kMetricPanPartialOffset;
     double *ms_part = pan_part + (int64_t)kMetricMaxCtas * kMetricStride;
     int gp = 0, gm = 0;
     cudaError_t e;
-    // PAN-resolution pass
-    if (fast) {
+    // PAN-resolution pass (unless the fused forward + metrics kernel wrote it)
+    if (m.pan_done) {
+        gp = m.pan_ctas;
+        e = cudaSuccess;
+    } else if (fast) {
         const FastFn fp = fast_fn(false, m.bands, m.a16 != 0);
         const int64_t items = ((m.W + kStrip - 1) / kStrip) * ((m.H + kWin - 1) / kWin);
         e = fast_grid(fp, items, &gp);
@@ -1107,7 +1094,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     }
     if (e != cudaSuccess) return e;
     const int64_t nwp = (m.H / kWin) * (m.W / kWin), nwm = (m.H / 2 / kWin) * (m.W / 2 / kWin);
-    metrics_finalize_kernel<<<1, 256, 0, stream>>>(pan_part, ms_part, gp, gm, kMetricStride, m.bands,
+    metrics_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(pan_part, ms_part, gp, gm, kMetricStride, m.bands,
                                                    m.want_q, m.H, m.W, nwp, nwm, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
