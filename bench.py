@@ -5,15 +5,21 @@ Workload (one step): Daubechies-4 fusion of a Landsat-7-shaped synthetic scene,
 PAN 16384 x 16384 uint8 with 6 MS bands 8192 x 8192 uint8 (periodic wrap, LL
 gain 2), writing every fused band both as float32 and as rounded uint8 in one
 pass, then ERGAS and QNR of the uint8 product on the GPU.  Inputs are
-generated on the device from a seed (scenegen).
+generated on the device from a seed (scenegen).  The step is the library's
+fused form: dwtfuse_fuse_and_score (the forward, scoring its uint8 product on
+chip) then dwtfuse_score_finish (MS-resolution pass and reduction).
 
   value     fused Gpx/s = PAN pixels x bands per second, inputs resident in HBM
   e2e       the same metric with the inputs copied host -> device from pinned
             memory and the uint8 fused bands and quality figures copied back
             every step (copies and compute of neighbouring steps overlap)
-  roofline  fused-forward kernel: algorithmic bytes per launch / mean launch
-            time (CUDA events on the launch stream) against the measured HBM
-            copy bandwidth
+  roofline  the forward-and-score kernel: algorithmic bytes per launch (inputs
+            read once, both outputs written once) / mean launch time (CUDA
+            events on the launch stream) against the measured HBM copy
+            bandwidth
+  separate  the same step as two separate calls (dwtfuse_fuse, then
+            dwtfuse_metrics reading the product back), with the plain
+            forward's roofline
   forms     the other forms of the path, timed after the main region on their
             own workloads: 96 uneven scenes through one captured batched launch;
             forward + backward of a batch of 8 float32 4096^2 scenes (4 bands)
@@ -50,18 +56,17 @@ WAVELET = 1  # Daubechies-4
 BLOB_SCALE = 16.0
 FALLBACK_HBM_GBS = 6800.0
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the fused forward
-# at this workload, keyed by the hash of the kernel sources it was taken on.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the
+# forward-and-score kernel at this workload, keyed by the hash of the kernel
+# sources it was taken on.
 KNOWN_TRAFFIC: dict[str, float] = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
-    # read 694,831,360 + write 7,991,928,320 (profiles/fuse_fwd_d4_4096x4096_b6.md)
-    "c468ee287701": 8686759680.0,
 }
+KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
 
 def kernel_hash() -> str:
     h = hashlib.sha1()
-    for f in ("fuse_tile.cuh", "fuse_fwd.cu"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1803_00737_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -292,8 +297,7 @@ def measure_e2e(args, pan, ms, out_f, mws, stream, world, dev) -> dict:
         with torch.cuda.stream(s_cmp):
             s_cmp.wait_event(uploaded[i])
             s_cmp.wait_event(downloaded[i])       # download k-2 is done with this output set
-            _C.dwtfuse_fuse(pan_d[i], ms_d[i], WAVELET, out_f, out_u[i], stream=s_cmp)
-            _C.dwtfuse_metrics(out_u[i], ms_d[i], pan_d[i], mws, res_d[i], stream=s_cmp)
+            _C.dwtfuse_fuse_metrics(pan_d[i], ms_d[i], WAVELET, out_f, out_u[i], mws, res_d[i], stream=s_cmp)
             computed[i].record(s_cmp)
         with torch.cuda.stream(s_out):
             s_out.wait_event(computed[i])
@@ -575,18 +579,18 @@ def run_ours(args) -> None:
     res = torch.zeros(4, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def fwd():
-        _C.dwtfuse_fuse(pan, ms, WAVELET, out_f, out_u)
+    def fwd():  # forward + on-chip scoring: one kernel launch
+        _C.dwtfuse_fuse_and_score(pan, ms, WAVELET, out_f, out_u, mws)
 
-    def metrics():
-        _C.dwtfuse_metrics(out_u, ms, pan, mws, res)
+    def metrics():  # MS-resolution pass + finalize
+        _C.dwtfuse_score_finish(ms, pan, out_u, mws, res)
 
     def step():
         fwd()
         metrics()
 
-    fwd_launches = (BANDS + 7) // 8
-    launches_per_step = fwd_launches + 3  # + metric passes at PAN and MS size, finalize
+    fwd_launches = 1
+    launches_per_step = fwd_launches + 2
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -621,6 +625,14 @@ def run_ours(args) -> None:
     max_el, total_units = aggregate(elapsed, units, world, dev)
     value = total_units / max_el / 1e9
 
+    # The same step as separate calls, for comparison (not the headline).
+    res_sep = torch.zeros(4, dtype=torch.float64, device=dev)
+    f_sep = _time_ms(lambda: _C.dwtfuse_fuse(pan, ms, WAVELET, out_f, out_u), K, stream)
+    m_sep = _time_ms(lambda: _C.dwtfuse_metrics(out_u, ms, pan, mws, res_sep), K, stream)
+    separate = {"fwd_ms": f_sep, "metrics_ms": m_sep, "step_ms": f_sep + m_sep,
+                "fwd_roofline_frac": fwd_bytes_per_launch() / (f_sep / 1e3) / 1e9 / measured_hbm()[0],
+                "quality_equal_to_fused": bool(torch.allclose(res_sep, res, rtol=0, atol=1e-6))}
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args, pan, ms, out_f, mws, stream, world, dev)
@@ -632,7 +644,7 @@ def run_ours(args) -> None:
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": KNOWN_TRAFFIC.get(kh),
                 "peak_source": f"{peak_kind} (copy bandwidth)",
-                "kernel": "fuse_fwd_kernel<uint8, D4, 6>", "kernel_hash": kh,
+                "kernel": "fuse_metrics_kernel<uint8, D4, 6> (forward + on-chip scoring)", "kernel_hash": kh,
                 "algorithmic_bytes_per_launch": fwd_bytes_per_launch(),
                 "mean_launch_ms": mean_fwd_s * 1e3}
 
@@ -665,6 +677,7 @@ def run_ours(args) -> None:
             "fwd_ms": {"mean": statistics.mean(fwd_ms), "min": min(fwd_ms), "max": max(fwd_ms)},
             "metrics_ms": {"mean": statistics.mean(met_ms), "min": min(met_ms), "max": max(met_ms)},
             "fwd_only_gpxs": H * W * BANDS / (statistics.mean(fwd_ms) / 1e3) / 1e9,
+            "separate": separate,
             "quality": dict(zip(["ERGAS", "QNR", "D_lambda", "D_s"], quality)),
             "forms": forms,
         }))

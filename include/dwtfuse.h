@@ -194,6 +194,23 @@ int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int6
                          int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
                          size_t ws_bytes, double *out_device, void *stream);
 
+/*
+ * dwtfuse_fuse_metrics in two calls on the same workspace, for callers that
+ * schedule or time the halves apart.  dwtfuse_fuse_and_score launches only
+ * the fused forward that scores its product (uint8 inputs, <= 6 bands; else
+ * DWTFUSE_ESHAPE) and leaves the partial scores in the workspace;
+ * dwtfuse_score_finish then runs the MS-resolution pass and the reduction
+ * into out_device.  The second call must follow the first on the same
+ * stream (or after it), with the same ms, pan, bands, H, W and out_u8, and no
+ * other metrics call on that workspace in between.
+ */
+int dwtfuse_fuse_and_score(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                           int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
+                           size_t ws_bytes, void *stream);
+int dwtfuse_score_finish(const void *const *ms, const void *pan, int in_dtype, int bands, int64_t H,
+                         int64_t W, const uint8_t *out_u8, void *workspace, size_t ws_bytes,
+                         double *out_device, void *stream);
+
 /* One scene of a batched call (all pointers on the device, as above). */
 typedef struct {
     const void *pan;

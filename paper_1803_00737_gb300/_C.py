@@ -72,6 +72,9 @@ _SIGS = {
                              _vp, _vp]),
     "dwtfuse_fuse_metrics": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp, _sz,
                                   _vp, _vp]),
+    "dwtfuse_fuse_and_score": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp, _sz,
+                                    _vp]),
+    "dwtfuse_score_finish": (_i, [ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _vp, _vp, _sz, _vp, _vp]),
     "dwtfuse_ergas": (_i, [_vp, _i, ctypes.POINTER(_vp), _i, _i, _i64, _i64, _vp, _sz,
                            ctypes.POINTER(ctypes.c_double), _vp]),
     "dwtfuse_qnr": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
@@ -278,11 +281,7 @@ def dwtfuse_metrics(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch
     _check(st, "dwtfuse_metrics")
 
 
-def dwtfuse_fuse_metrics(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
-                         out_u8: torch.Tensor, workspace: torch.Tensor, out_device: torch.Tensor,
-                         stream=None) -> None:
-    """Fused forward into the caller's outputs, then ERGAS, QNR, D_lambda, D_s
-    of the uint8 product into out_device[0:4] (async; see dwtfuse.h)."""
+def _fuse_score_args(pan: torch.Tensor, ms, out_f32, out_u8):
     bands = _bands(ms)
     H, W = pan.shape
     ptrs = (_vp * len(bands))(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
@@ -292,15 +291,51 @@ def dwtfuse_fuse_metrics(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Ten
     for name, o, dt in (("out_f32", out_f32, torch.float32), ("out_u8", out_u8, torch.uint8)):
         if o is not None and (o.dtype != dt or tuple(o.shape) != (len(bands), H, W)):
             raise ValueError(f"{name} must be {dt} of shape ({len(bands)}, {H}, {W})")
+    return bands, H, W, ptrs
+
+
+def _out_device(out_device: torch.Tensor):
     if out_device.dtype != torch.float64 or out_device.numel() < 4:
         raise ValueError("out_device must be a float64 CUDA tensor with >= 4 elements")
+    return _dev(out_device, "out_device")
+
+
+def dwtfuse_fuse_metrics(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
+                         out_u8: torch.Tensor, workspace: torch.Tensor, out_device: torch.Tensor,
+                         stream=None) -> None:
+    """Fused forward into the caller's outputs, then ERGAS, QNR, D_lambda, D_s
+    of the uint8 product into out_device[0:4] (async; see dwtfuse.h)."""
+    bands, H, W, ptrs = _fuse_score_args(pan, ms, out_f32, out_u8)
     st = lib().dwtfuse_fuse_metrics(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet),
                                     _dtype_code(pan, "pan"),
                                     _dev(out_f32, "out_f32") if out_f32 is not None else None,
                                     _dev(out_u8, "out_u8"), _dev(workspace, "workspace"),
                                     workspace.numel() * workspace.element_size(),
-                                    _dev(out_device, "out_device"), _stream(stream))
+                                    _out_device(out_device), _stream(stream))
     _check(st, "dwtfuse_fuse_metrics")
+
+
+def dwtfuse_fuse_and_score(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
+                           out_u8: torch.Tensor, workspace: torch.Tensor, stream=None) -> None:
+    """First half of dwtfuse_fuse_metrics: the forward that scores its product."""
+    bands, H, W, ptrs = _fuse_score_args(pan, ms, out_f32, out_u8)
+    st = lib().dwtfuse_fuse_and_score(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet),
+                                      _dtype_code(pan, "pan"),
+                                      _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                                      _dev(out_u8, "out_u8"), _dev(workspace, "workspace"),
+                                      workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(st, "dwtfuse_fuse_and_score")
+
+
+def dwtfuse_score_finish(ms, pan: torch.Tensor, out_u8: torch.Tensor, workspace: torch.Tensor,
+                         out_device: torch.Tensor, stream=None) -> None:
+    """Second half of dwtfuse_fuse_metrics: MS-resolution pass and reduction."""
+    bands, H, W, ptrs = _fuse_score_args(pan, ms, None, out_u8)
+    st = lib().dwtfuse_score_finish(ptrs, _dev(pan, "pan"), _dtype_code(pan, "pan"), len(bands), H, W,
+                                    _dev(out_u8, "out_u8"), _dev(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(),
+                                    _out_device(out_device), _stream(stream))
+    _check(st, "dwtfuse_score_finish")
 
 
 def dwtfuse_ergas(fused: torch.Tensor, ms, workspace: torch.Tensor, stream=None) -> float:

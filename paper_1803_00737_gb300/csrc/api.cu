@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <map>
 #include <unordered_map>
 
 #include "dwtfuse.h"
@@ -13,6 +14,7 @@ namespace dwtfuse {
 namespace {
 std::mutex g_mu;
 std::unordered_map<const void *, int> g_occ;
+std::map<std::pair<int, const void *>, int> g_occ_smem;
 std::unordered_map<int, int> g_sms;
 std::atomic<int> g_rows{0};  // 0: balanced_rows() per launch
 thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -33,6 +35,31 @@ cudaError_t resident_blocks(const void *fn, int threads, int *out) {
     if (occ < 1) occ = 1;
     std::lock_guard<std::mutex> lk(g_mu);
     g_occ[fn] = occ;
+    *out = occ;
+    return cudaSuccess;
+}
+
+cudaError_t resident_blocks_smem(const void *fn, int threads, int smem, int *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const std::pair<int, const void *> key{dev, fn};
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_occ_smem.find(key);
+        if (it != g_occ_smem.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_occ_smem[key] = occ;
     *out = occ;
     return cudaSuccess;
 }
@@ -278,26 +305,63 @@ int dwtfuse_metrics(const void *fused, int fused_dtype, const void *const *ms, c
     return cuda_status(launch_metrics(m, static_cast<cudaStream_t>(stream)));
 }
 
+// Validates a fused forward + metrics call (the two halves share it).
+static int make_fuse_score(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                           int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
+                           size_t ws_bytes, SceneArgs *s, MetricLaunch *m) {
+    if (!out_u8) return DWTFUSE_EINVAL;
+    int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, s);
+    if (st != DWTFUSE_OK) return st;
+    return make_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, bands, H, W, kMetricWindow, true, workspace,
+                        ws_bytes, m);
+}
+
+int dwtfuse_fuse_and_score(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
+                           int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
+                           size_t ws_bytes, void *stream) {
+    SceneArgs s;
+    MetricLaunch m;
+    const int st = make_fuse_score(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, workspace,
+                                   ws_bytes, &s, &m);
+    if (st != DWTFUSE_OK) return st;
+    if (!fuse_metrics_supported(s)) return DWTFUSE_ESHAPE;
+    return cuda_status(launch_fuse_metrics(s, m.workspace + kMetricPanPartialOffset, kMetricStride,
+                                           reinterpret_cast<int *>(m.workspace + kMetricPanCtasSlot),
+                                           static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_score_finish(const void *const *ms, const void *pan, int in_dtype, int bands, int64_t H,
+                         int64_t W, const uint8_t *out_u8, void *workspace, size_t ws_bytes,
+                         double *out_device, void *stream) {
+    if (!out_device) return DWTFUSE_EINVAL;
+    if (!aligned(out_device, 8)) return DWTFUSE_EALIGN;
+    MetricLaunch m;
+    const int st = make_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, bands, H, W, kMetricWindow, true,
+                                workspace, ws_bytes, &m);
+    if (st != DWTFUSE_OK) return st;
+    if (in_dtype != DWTFUSE_U8 || bands > kFuseMetricsMaxBands) return DWTFUSE_ESHAPE;
+    m.result = out_device;
+    m.pan_done = 1;
+    return cuda_status(launch_metrics(m, static_cast<cudaStream_t>(stream)));
+}
+
 int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
                          int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
                          size_t ws_bytes, double *out_device, void *stream) {
-    if (!out_u8 || !out_device) return DWTFUSE_EINVAL;
+    if (!out_device) return DWTFUSE_EINVAL;
     if (!aligned(out_device, 8)) return DWTFUSE_EALIGN;
     SceneArgs s;
-    int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
-    if (st != DWTFUSE_OK) return st;
     MetricLaunch m;
-    st = make_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, bands, H, W, kMetricWindow, true, workspace,
-                      ws_bytes, &m);
+    const int st = make_fuse_score(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, workspace,
+                                   ws_bytes, &s, &m);
     if (st != DWTFUSE_OK) return st;
     m.result = out_device;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (fuse_metrics_supported(s)) {
-        int ctas = 0;
-        e = launch_fuse_metrics(s, m.workspace + kMetricPanPartialOffset, kMetricStride, &ctas, cs);
+        e = launch_fuse_metrics(s, m.workspace + kMetricPanPartialOffset, kMetricStride,
+                                reinterpret_cast<int *>(m.workspace + kMetricPanCtasSlot), cs);
         m.pan_done = 1;
-        m.pan_ctas = ctas;
     } else {
         e = launch_fuse(s, rows_per_item(), 0, cs);
     }

@@ -214,8 +214,8 @@ struct MetricEmit {
 
 template <typename T, int WAV, int NB>
 __global__ void __launch_bounds__(kFmThreads, 2)
-fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int stride, int64_t strips_x,
-                    int64_t items, int R) {
+fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int stride, int *ctas_out,
+                    int64_t strips_x, int64_t items, int R) {
     using L = FmLayout<NB>;
     extern __shared__ __align__(16) unsigned char fm_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -225,6 +225,7 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
     int *sums = reinterpret_cast<int *>(rep + L::kRep);
     float *qs = reinterpret_cast<float *>(sums + L::kSums);
     long long *se64 = reinterpret_cast<long long *>(wb + L::kWords * 4);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ctas_out = (int)gridDim.x;  // partial rows, for the finalize
     for (int k = 0; k < L::NS; ++k) sums[k * 32 + lane] = 0;
     for (int k = lane; k < L::kQ; k += 32) qs[k] = 0.f;
     for (int b = 0; b < NB; ++b) se64[b * 32 + lane] = 0;
@@ -290,17 +291,14 @@ bool fuse_metrics_supported(const SceneArgs &s) {
     return !s.in_f32 && s.out_u8 != nullptr && s.bands >= 1 && s.bands <= kFuseMetricsMaxBands;
 }
 
-cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas,
+cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas_dev,
                                 cudaStream_t stream) {
     int smem = 0;
     void *fn = fm_kernel_ptr(s.wavelet, s.bands, &smem);
     if (fn == nullptr || s.in_f32 || s.out_u8 == nullptr) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     int occ = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFmThreads, smem);
+    cudaError_t e = resident_blocks_smem(fn, kFmThreads, smem, &occ);
     if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
     const int64_t cap = (int64_t)sms * occ;
@@ -320,11 +318,10 @@ cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int str
     if (grid > cap) grid = cap;
     if (grid > kMetricMaxCtas) grid = kMetricMaxCtas;
     if (grid < 1) grid = 1;
-    *ctas = (int)grid;
     SceneArgs sa = s;
     int64_t strips_x = g.strips_x, items = g.items;
     int strd = stride, Rv = R;
-    void *args[] = {&sa, &pan_partial, &strd, &strips_x, &items, &Rv};
+    void *args[] = {&sa, &pan_partial, &strd, &ctas_dev, &strips_x, &items, &Rv};
     return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kFmThreads), args, (size_t)smem, stream);
 }
 

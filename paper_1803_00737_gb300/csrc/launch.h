@@ -47,8 +47,9 @@ struct MetricLaunch {
     int32_t a32_ms;     // uint8 MS-pass fast path: W % 32 == 0, PAN and MS 16-byte aligned
     double *workspace;  // kMetricWorkspaceBytes, 8-byte aligned
     double *result;     // device pointer for the 4 results, or nullptr
-    int32_t pan_done;   // PAN-resolution partial rows already written (fused forward + metrics)
-    int32_t pan_ctas;   // ... and how many
+    int32_t pan_done;   // PAN-resolution partial rows already written (fused forward + metrics),
+                        // their count at kMetricPanCtasSlot
+    int32_t pad_;
 };
 
 // Fused forward + PAN-resolution metrics (fuse_metrics.cu): uint8 inputs, a
@@ -89,6 +90,10 @@ struct DwtLaunch {
 
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);
+// Resident CTAs per SM with `smem` bytes of dynamic shared memory; the first
+// call per device and kernel also raises the kernel's dynamic shared memory
+// limit to `smem` (cached: later launches make no attribute or occupancy call).
+cudaError_t resident_blocks_smem(const void *fn, int threads, int smem, int *out);
 // SM count of the current device (cached per device).
 cudaError_t sm_count(int *out);
 
@@ -98,10 +103,13 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
 cudaError_t launch_dwt2(const DwtLaunch &d, cudaStream_t stream);
 cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream);
 bool fuse_metrics_supported(const SceneArgs &s);
-// Writes the PAN-resolution partial rows (stride doubles apart) and their count.
-cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas,
+// Writes the PAN-resolution partial rows (stride doubles apart) and their
+// count (device int at ctas_dev).
+cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int stride, int *ctas_dev,
                                 cudaStream_t stream);
-// Offset of the PAN-resolution partial rows in the metrics workspace (doubles).
+// Metrics workspace: doubles [0, 4) results, the int at double 4 the count of
+// PAN-resolution partial rows written by the fused kernel, rows from double 8.
+constexpr int64_t kMetricPanCtasSlot = 4;
 constexpr int64_t kMetricPanPartialOffset = 8;
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);

@@ -889,9 +889,10 @@ metrics_ms_kernel(const __grid_constant__ MetricArgs a) {
 // is a few hundred cycles.
 constexpr int kFinalizeThreads = 1024;
 __global__ void __launch_bounds__(kFinalizeThreads)
-metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, int ctas_ms,
-                        int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
+metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, const int *ctas_pan_dev,
+                        int ctas_ms, int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
                         int64_t nwin_ms, double *out) {
+    if (ctas_pan_dev) ctas_pan = *ctas_pan_dev;
     __shared__ double tot_pan[64 + kMaxBands];
     __shared__ double tot_ms[64 + kMaxBands];
     const int P = nb * (nb - 1) / 2 + nb;
@@ -986,14 +987,11 @@ FastFn fast_fn(bool ms_pass, int nb, bool aligned) {
 // most of shared memory), at most kMetricMaxCtas.
 cudaError_t fast_grid(const FastFn &f, int64_t items, int *grid) {
     static_assert(kMetricMaxCtas >= 1, "");
-    cudaError_t e = cudaFuncSetAttribute(f.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem);
-    if (e != cudaSuccess) return e;
     int occ = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f.fn, f.warps * 32, f.smem);
+    cudaError_t e = resident_blocks_smem(f.fn, f.warps * 32, f.smem, &occ);
     if (e != cudaSuccess) return e;
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
     int64_t g = (items + f.warps - 1) / f.warps;
     const int64_t cap = (int64_t)sms * occ;
     if (g > cap) g = cap;
@@ -1054,7 +1052,6 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     cudaError_t e;
     // PAN-resolution pass (unless the fused forward + metrics kernel wrote it)
     if (m.pan_done) {
-        gp = m.pan_ctas;
         e = cudaSuccess;
     } else if (fast) {
         const FastFn fp = fast_fn(false, m.bands, m.a16 != 0);
@@ -1094,8 +1091,9 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     }
     if (e != cudaSuccess) return e;
     const int64_t nwp = (m.H / kWin) * (m.W / kWin), nwm = (m.H / 2 / kWin) * (m.W / 2 / kWin);
-    metrics_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(pan_part, ms_part, gp, gm, kMetricStride, m.bands,
-                                                   m.want_q, m.H, m.W, nwp, nwm, out);
+    const int *gp_dev = m.pan_done ? reinterpret_cast<const int *>(m.workspace + kMetricPanCtasSlot) : nullptr;
+    metrics_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(pan_part, ms_part, gp, gp_dev, gm, kMetricStride,
+                                                                m.bands, m.want_q, m.H, m.W, nwp, nwm, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (m.result && m.result != out)

@@ -150,3 +150,25 @@ def test_graph_capture(ws):
     torch.cuda.synchronize()
     _, _, r2 = separate_path(pan, ms, O.D4, ws)
     agree(res.cpu().numpy(), r2)
+
+
+def test_two_call_form(ws):
+    """dwtfuse_fuse_and_score then dwtfuse_score_finish = dwtfuse_fuse_metrics."""
+    pan, ms = scene(192, 1030, 6, seed=21)
+    B, (H, W) = ms.shape[0], pan.shape
+    ou = torch.empty((B, H, W), dtype=torch.uint8, device=DEV)
+    of = torch.empty((B, H, W), device=DEV)
+    res = torch.full((4,), float("nan"), dtype=torch.float64, device=DEV)
+    _C.dwtfuse_fuse_and_score(pan, ms, O.D4, of, ou, ws)
+    _C.dwtfuse_score_finish(ms, pan, ou, ws, res)
+    torch.cuda.synchronize()
+    f1, u1, r1 = fused_path(pan, ms, O.D4, ws)
+    assert torch.equal(of, f1) and torch.equal(ou, u1)
+    assert np.array_equal(res.cpu().numpy(), r1)
+
+
+def test_two_call_form_rejects_unsupported(ws):
+    pan, ms = scene(64, 96, 7, seed=2)
+    ou = torch.empty((7, 64, 96), dtype=torch.uint8, device=DEV)
+    with pytest.raises(_C.DwtfuseError):
+        _C.dwtfuse_fuse_and_score(pan, ms, O.D4, None, ou, ws)
