@@ -909,26 +909,36 @@ metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_
         if (lane == 0) (ms ? tot_ms : tot_pan)[kk] = a;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const double n = (double)H * (double)W, nms = (double)(H / 2) * (double)(W / 2);
-    double acc = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        const double mse = tot_pan[P + b] / n, mu = tot_ms[P + b] / nms;
-        acc += mse / (mu * mu);
+    if (threadIdx.x >= 32) return;
+    // The FP64 divisions of the figures run one per lane (the FP64 pipe is
+    // narrow; in one thread they would take most of this kernel's time), then
+    // fixed butterflies sum them (the same order on every run).
+    const int NBB = nb * (nb - 1) / 2;
+    const bool q_ok = want_q && nwin_pan >= 1 && nwin_ms >= 1;
+    double e = 0.0, dl = 0.0, ds = 0.0;
+    if (lane < nb) {
+        const double mse = tot_pan[P + lane] / ((double)H * (double)W);
+        const double mu = tot_ms[P + lane] / ((double)(H / 2) * (double)(W / 2));
+        e = mse / (mu * mu);
     }
-    out[0] = 100.0 * 0.5 * sqrt(acc / nb);
-    if (!want_q || nwin_pan < 1 || nwin_ms < 1) {
+    if (q_ok) {
+        for (int k = lane; k < P; k += 32) {  // up to 36 pairs (8 bands)
+            const double d = fabs(tot_pan[k] / (double)nwin_pan - tot_ms[k] / (double)nwin_ms);
+            if (k < NBB) dl += d; else ds += d;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        dl += __shfl_xor_sync(0xffffffffu, dl, o);
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+    }
+    if (lane != 0) return;
+    out[0] = 100.0 * 0.5 * sqrt(e / nb);
+    if (!q_ok) {
         out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
         return;
     }
-    double dl = 0.0;
-    int idx = 0;
-    for (int b = 0; b < nb; ++b)
-        for (int c = b + 1; c < nb; ++c, ++idx)
-            dl += fabs(tot_pan[idx] / nwin_pan - tot_ms[idx] / nwin_ms);
     dl = nb > 1 ? 2.0 * dl / (nb * (nb - 1)) : 0.0;
-    double ds = 0.0;
-    for (int b = 0; b < nb; ++b, ++idx) ds += fabs(tot_pan[idx] / nwin_pan - tot_ms[idx] / nwin_ms);
     ds /= nb;
     out[1] = (1.0 - dl) * (1.0 - ds);
     out[2] = dl;
