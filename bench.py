@@ -60,6 +60,9 @@ FALLBACK_HBM_GBS = 6800.0
 # forward-and-score kernel at this workload, keyed by the hash of the kernel
 # sources it was taken on.
 KNOWN_TRAFFIC: dict[str, float] = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
+    # read 689,938,176 + write 7,991,649,280 (profiles/fuse_metrics_d4_4096x4096_b6.md)
+    "2c9869a1b778": 8681587456.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
