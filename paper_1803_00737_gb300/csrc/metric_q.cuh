@@ -10,6 +10,13 @@ namespace dwtfuse {
 
 constexpr int kQWinPx = 32 * 32;  // pixels per window
 
+// Position of band pair (b, c), b < c < nb, among the pair sums (b-major
+// order); the band-PAN pairs follow at nb(nb-1)/2 + b.  Loops over pairs run
+// b and c over [0, nb) with a `c > b` test, so that both have constant trip
+// counts, unroll fully, and the position is a compile-time constant (a
+// triangular inner loop stays a loop and its sums go to local memory).
+__host__ __device__ constexpr int pair_index(int nb, int b, int c) { return b * nb - b * (b + 1) / 2 + (c - b - 1); }
+
 // Q of one window, given exact integer sums (8-bit data).  ys = scale of y.
 __device__ __forceinline__ float q_exact(long long sx, long long sxx, long long sy, long long syy,
                                          long long sxy, int ys) {

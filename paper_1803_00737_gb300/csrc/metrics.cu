@@ -124,13 +124,13 @@ __device__ __forceinline__ void accumulate_pixel(const A *v, A *s1, A *s2, A *sx
         s1[k] += v[k];
         s2[k] += v[k] * v[k];
     }
-    int idx = 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] += v[b] * v[c];
+        for (int c = 0; c < NB; ++c)
+            if (c > b) sxy[pair_index(NB, b, c)] += v[b] * v[c];
 #pragma unroll
-    for (int b = 0; b < NB; ++b, ++idx) sxy[idx] += v[b] * v[NB];
+    for (int b = 0; b < NB; ++b) sxy[NB * (NB - 1) / 2 + b] += v[b] * v[NB];
 }
 
 // After a strip: window sums over the 8 lanes of each window (every lane of
@@ -147,15 +147,13 @@ __device__ __forceinline__ void finish_strip(const A *s1, const A *s2, const A *
         S1[k] = xor_sum8(s1[k]);
         S2[k] = xor_sum8(s2[k]);
     }
-    int idx = 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
 #pragma unroll
-        for (int c = b + 1; c <= NB; ++c) {
+        for (int c = 0; c < NB; ++c) {
             // pairs in the order of accumulate_pixel: band-band first, then band-PAN
-            const int p = (c < NB) ? idx : -1;
-            if (c < NB) ++idx;
-            if (p < 0) continue;
+            if (c <= b) continue;
+            const int p = pair_index(NB, b, c);
             const A Sxy = xor_sum8(sxy[p]);
             const float q = exact ? q_exact((long long)S1[b], (long long)S2[b], (long long)S1[c],
                                             (long long)S2[c], (long long)Sxy, 1)
@@ -164,7 +162,8 @@ __device__ __forceinline__ void finish_strip(const A *s1, const A *s2, const A *
         }
     }
 #pragma unroll
-    for (int b = 0; b < NB; ++b, ++idx) {
+    for (int b = 0; b < NB; ++b) {
+        const int idx = NB * (NB - 1) / 2 + b;
         const A Sxy = xor_sum8(sxy[idx]);
         const float q = exact ? q_exact((long long)S1[b], (long long)S2[b], (long long)S1[NB],
                                         (long long)S2[NB], (long long)Sxy, ys)
@@ -514,13 +513,19 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
                         s1[k] = __dp4a(v[k], 0x01010101, s1[k]);
                         s2[k] = __dp4a(v[k], v[k], s2[k]);
                     }
-                    int idx = 0;
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
 #pragma unroll
-                        for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+                        for (int c = 0; c < NB; ++c)
+                            if (c > b) {
+                                const int idx = pair_index(NB, b, c);
+                                sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+                            }
 #pragma unroll
-                    for (int b = 0; b < NB; ++b, ++idx) sxy[idx] = __dp4a(v[b], v[NB], sxy[idx]);
+                    for (int b = 0; b < NB; ++b) {
+                        const int idx = NB * (NB - 1) / 2 + b;
+                        sxy[idx] = __dp4a(v[b], v[NB], sxy[idx]);
+                    }
                 }
             }
         }
@@ -538,17 +543,19 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
         }
         const bool leader = full && (lane & 1) == 0;
         float *slotq = sq + (lane >> 1) * P;
-        int idx = 0;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int c = b + 1; c < NB; ++c, ++idx) {
+            for (int c = 0; c < NB; ++c) {
+                if (c <= b) continue;
+                const int idx = pair_index(NB, b, c);
                 const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
                 const float qv = q_exact(S1[b], S2[b], S1[c], S2[c], Sxy, 1);
                 if (leader) slotq[idx] += qv;
             }
 #pragma unroll
-        for (int b = 0; b < NB; ++b, ++idx) {
+        for (int b = 0; b < NB; ++b) {
+            const int idx = NB * (NB - 1) / 2 + b;
             const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
             const float qv = q_exact(S1[b], S2[b], S1[NB], S2[NB], Sxy, 1);
             if (leader) slotq[idx] += qv;
@@ -723,13 +730,17 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
                     s1[NB] += z[t];
                     s2[NB] += z[t] * z[t];
                 }
-                int idx = 0;
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
-                    for (int c = b + 1; c < NB; ++c, ++idx) sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+                    for (int c = 0; c < NB; ++c)
+                        if (c > b) {
+                            const int idx = pair_index(NB, b, c);
+                            sxy[idx] = __dp4a(v[b], v[c], sxy[idx]);
+                        }
 #pragma unroll
-                for (int b = 0; b < NB; ++b, ++idx) {
+                for (int b = 0; b < NB; ++b) {
+                    const int idx = NB * (NB - 1) / 2 + b;
                     // signed bytes of v[b] times Z
                     const int w = v[b];
                     sxy[idx] += ((w << 24) >> 24) * z[0] + ((w << 16) >> 24) * z[1] +
@@ -749,17 +760,19 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
         }
         const bool leader = full && (lane & 1) == 0;
         float *slotq = sq + (lane >> 1) * P;
-        int idx = 0;
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int c = b + 1; c < NB; ++c, ++idx) {
+            for (int c = 0; c < NB; ++c) {
+                if (c <= b) continue;
+                const int idx = pair_index(NB, b, c);
                 const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
                 const float qv = q_exact(S1[b], S2[b], S1[c], S2[c], Sxy, 1);
                 if (leader) slotq[idx] += qv;
             }
 #pragma unroll
-        for (int b = 0; b < NB; ++b, ++idx) {
+        for (int b = 0; b < NB; ++b) {
+            const int idx = NB * (NB - 1) / 2 + b;
             const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
             const float qv = q_exact(S1[b], S2[b], S1[NB], S2[NB], Sxy, 4);
             if (leader) slotq[idx] += qv;
