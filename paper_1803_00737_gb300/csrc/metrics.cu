@@ -297,20 +297,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Bytes outside the image plane [lo, hi) are never read: a chunk crossing
 // hi is zero-filled past it; a chunk starting before lo (a plane that is
 // not 16-byte aligned) is copied byte by byte.
-__device__ __forceinline__ void copy_row(unsigned char *dst, const uint8_t *a0, int span,
-                                         const uint8_t *lo, const uint8_t *hi, int lane) {
-    const uintptr_t ua = reinterpret_cast<uintptr_t>(a0);
-    const uint8_t *c0 = reinterpret_cast<const uint8_t *>(ua & ~(uintptr_t)15);
-    const int nchunks = ((int)(ua & 15) + span + 15) >> 4;
-    if (c0 >= lo && c0 + 16 * nchunks <= hi) {
-        // the whole span lies inside the plane (every row but a plane's last)
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {  // up to 96 chunks: 1024 staged bytes + slack
-            const int k = lane + 32 * t;
-            if (k < nchunks) cp_async16(dst + 16 * k, c0 + 16 * k, 16u);
-        }
-        return;
-    }
+// Plane edges (out of line: rare, and inlined at every row copy it would
+// crowd the instruction cache).
+static __device__ __noinline__ void copy_row_edge(unsigned char *dst, const uint8_t *c0, int nchunks,
+                                                  const uint8_t *lo, const uint8_t *hi, int lane) {
     for (int k = lane; k < nchunks; k += 32) {
         const uint8_t *src = c0 + 16 * k;
         if (src >= hi || src + 16 <= lo) continue;
@@ -324,8 +314,30 @@ __device__ __forceinline__ void copy_row(unsigned char *dst, const uint8_t *a0, 
     }
 }
 
+template <int MAXCH>  // most chunks a row can have (a bound known at compile time)
+__device__ __forceinline__ void copy_row(unsigned char *dst, const uint8_t *a0, int span,
+                                         const uint8_t *lo, const uint8_t *hi, int lane) {
+    const uintptr_t ua = reinterpret_cast<uintptr_t>(a0);
+    const uint8_t *c0 = reinterpret_cast<const uint8_t *>(ua & ~(uintptr_t)15);
+    const int nchunks = ((int)(ua & 15) + span + 15) >> 4;
+    if (c0 >= lo && c0 + 16 * nchunks <= hi) {
+        // the whole span lies inside the plane (every row but a plane's first or last)
+#pragma unroll
+        for (int t = 0; t < (MAXCH + 31) / 32; ++t) {
+            const int k = lane + 32 * t;
+            if (k < nchunks) cp_async16(dst + 16 * k, c0 + 16 * k, 16u);
+        }
+        return;
+    }
+    copy_row_edge(dst, c0, nchunks, lo, hi, lane);
+}
+
 // NW 32-bit words of a staged row starting at byte offset off (one offset per
-// image row, the same for every lane, so the branches are uniform).
+// image row, the same for every lane, so the branches are uniform).  Lanes
+// sit 4 NW bytes apart; an unaligned row is read as the aligned 16-byte (NW a
+// multiple of 4) or 8-byte (NW = 2) pieces that cover it, which keeps
+// consecutive lanes on consecutive banks, and the words are shifted into place
+// with uniform selects and funnel shifts.
 template <int NW>
 __device__ __forceinline__ void read_words(const unsigned char *base, int off, uint32_t *w) {
     if (NW % 4 == 0 && (off & 15) == 0) {
@@ -342,13 +354,34 @@ __device__ __forceinline__ void read_words(const unsigned char *base, int off, u
         w[1] = q.y;
         return;
     }
-    const uint32_t *p = reinterpret_cast<const uint32_t *>(base + (off & ~3));
     const int sh = (off & 3) * 8;
-    uint32_t r[NW + 1];
+    if constexpr (NW % 4 == 0) {
+        const unsigned char *a = base + (off & ~15);
+        const int s = off & 15;
+        uint32_t r[NW + 4];
 #pragma unroll
-    for (int k = 0; k <= NW; ++k) r[k] = p[k];
+        for (int c = 0; c <= NW / 4; ++c) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(a + 16 * c);
+            r[4 * c] = q.x; r[4 * c + 1] = q.y; r[4 * c + 2] = q.z; r[4 * c + 3] = q.w;
+        }
+        uint32_t t[NW + 3];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = sh ? __funnelshift_r(r[k], r[k + 1], sh) : r[k];
+        for (int k = 0; k < NW + 3; ++k) t[k] = (s & 4) ? r[k + 1] : r[k];
+#pragma unroll
+        for (int k = 0; k <= NW; ++k) t[k] = (s & 8) ? t[k + 2] : t[k];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) w[k] = sh ? __funnelshift_r(t[k], t[k + 1], sh) : t[k];
+    } else {
+        static_assert(NW == 2, "read_words: NW is 2 or a multiple of 4");
+        const unsigned char *a = base + (off & ~7);
+        const uint2 q0 = *reinterpret_cast<const uint2 *>(a), q1 = *reinterpret_cast<const uint2 *>(a + 8);
+        const uint32_t r[4] = {q0.x, q0.y, q1.x, q1.y};
+        uint32_t t[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t[k] = (off & 4) ? r[k + 1] : r[k];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) w[k] = sh ? __funnelshift_r(t[k], t[k + 1], sh) : t[k];
+    }
 }
 
 // Byte mask keeping the first `v` bytes of word q of a lane (v may exceed 4q+3).
@@ -427,14 +460,15 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const uint8_t *plane = F + (int64_t)b * HW;
-                        copy_row(slot + b * kImgRow, plane + y * W + x0, span, plane, plane + HW, lane);
+                        copy_row<kStrip / 16 + 1>(slot + b * kImgRow, plane + y * W + x0, span, plane, plane + HW, lane);
                     }
-                    if (a.want_q) copy_row(slot + NB * kImgRow, pan + y * W + x0, span, pan, pan + HW, lane);
+                    if (a.want_q)
+                        copy_row<kStrip / 16 + 1>(slot + NB * kImgRow, pan + y * W + x0, span, pan, pan + HW, lane);
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
-                        copy_row(slot + K * kImgRow + b * kMsRow, m + (y >> 1) * W2 + (x0 >> 1), span / 2, m,
-                                 m + H2 * W2, lane);
+                        copy_row<kStrip / 32 + 1>(slot + K * kImgRow + b * kMsRow, m + (y >> 1) * W2 + (x0 >> 1),
+                                                  span / 2, m, m + H2 * W2, lane);
                     }
                 } else if (act) {
 #pragma unroll
@@ -639,12 +673,13 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
-                        copy_row(slot + b * kImgRow, m + i * W2 + j0, span, m, m + H2 * W2, lane);
+                        copy_row<kStrip / 16 + 1>(slot + b * kImgRow, m + i * W2 + j0, span, m, m + H2 * W2, lane);
                     }
                     if (any_full) {
-                        copy_row(slot + NB * kImgRow, pan + (2 * i) * W + 2 * j0, 2 * span, pan, pan + HW, lane);
-                        copy_row(slot + NB * kImgRow + PR, pan + (2 * i + 1) * W + 2 * j0, 2 * span, pan, pan + HW,
-                                 lane);
+                        copy_row<kStrip / 8 + 1>(slot + NB * kImgRow, pan + (2 * i) * W + 2 * j0, 2 * span, pan,
+                                                 pan + HW, lane);
+                        copy_row<kStrip / 8 + 1>(slot + NB * kImgRow + PR, pan + (2 * i + 1) * W + 2 * j0, 2 * span,
+                                                 pan, pan + HW, lane);
                     }
                 } else if (act) {
 #pragma unroll
