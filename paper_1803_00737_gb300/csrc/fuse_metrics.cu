@@ -71,6 +71,7 @@ struct MetricEmit {
     int64_t x0, m_s, m_e;
     int lane;
     bool a4;
+    bool alt;       // W % 4 == 2 with vector-aligned planes: even rows vectorised, odd rows shifted
     uint32_t keep;  // bytes of this lane's 4-pixel words inside the image
 
     __device__ __forceinline__ void band(int b, int64_t m, const float *v0, const float *v1, float mn,
@@ -82,9 +83,17 @@ struct MetricEmit {
         tile[(b * 4 + 2 * r + 1) * 32 + lane] = w1;
         // ERGAS reference: MS(m, n), MS(m, n+1) each repeated over 2 PAN columns.
         rep[(b * 2 + r) * 32 + lane] = __byte_perm(f2u8(mn), f2u8(mn1), 0x4400u);
-        if (!c.active) return;
         const int64_t HW = s.H * s.W;
         const int64_t o0 = (int64_t)b * HW + (2 * m) * s.W + c.x, o1 = o0 + s.W;
+        if (alt) {
+            // Even row on the 16-byte grid (the lane at x = W-2 writes pairs),
+            // odd row 2 pixels past it: every lane takes part in the shuffles.
+            OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)b * HW : nullptr, s.out_u8 + (int64_t)b * HW};
+            if (c.active) store4(o, (2 * m) * s.W + c.x, c.two, c.two, v0);
+            store4_shifted(o, (2 * m + 1) * s.W + c.x, lane, c.active, c.two, c.last, v1);
+            return;
+        }
+        if (!c.active) return;
         if (s.out_f32) {
             float *p0 = s.out_f32 + o0, *p1 = s.out_f32 + o1;
             if (a4) {
@@ -240,12 +249,13 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
         const LaneCols c = lane_cols(x0, lane, s.W);
         const int64_t x = x0 + 4 * lane;
         const uint32_t keep = x + 4 <= s.W ? 0xffffffffu : (x + 2 <= s.W ? 0x0000ffffu : 0u);
-        const bool a4 = s.a4 != 0;
-        MetricEmit<NB> out{s, c, tile, rep, sums, qs, se64, x0, m_s, m_e, lane, a4, keep};
+        const bool a4 = s.a4 != 0, alt = !a4 && s.alt != 0;
+        const bool lde = a4 || (alt && c.two);  // 4-pixel PAN loads on even rows
+        MetricEmit<NB> out{s, c, tile, rep, sums, qs, se64, x0, m_s, m_e, lane, a4, alt, keep};
         if (WAV == 0)
-            haar_rows<T, NB>(s, c, a4, a4, m_s, m_e, 0, NB, out);
+            haar_rows<T, NB>(s, c, lde, a4, m_s, m_e, 0, NB, out);
         else
-            d4_rows<T, NB>(s, c, a4, a4, m_s, m_e, 0, NB, out);
+            d4_rows<T, NB>(s, c, lde, a4, m_s, m_e, 0, NB, out);
     }
 
     // One partial row per CTA, in the layout of the PAN-resolution pass:
