@@ -61,8 +61,8 @@ FALLBACK_HBM_GBS = 6800.0
 # sources it was taken on.
 KNOWN_TRAFFIC: dict[str, float] = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
-    # read 689,938,176 + write 7,991,649,280 (profiles/fuse_metrics_d4_4096x4096_b6.md)
-    "2c9869a1b778": 8681587456.0,
+    # read 689,733,376 + write 7,991,625,984 (profiles/fuse_metrics_d4_4096x4096_b6.md)
+    "4230335fb78f": 8681359360.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
