@@ -362,6 +362,7 @@ int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int6
         e = launch_fuse_metrics(s, m.workspace + kMetricPanPartialOffset, kMetricStride,
                                 reinterpret_cast<int *>(m.workspace + kMetricPanCtasSlot), cs);
         m.pan_done = 1;
+        m.ms_early = 1;  // the MS pass follows our own fused kernel directly
     } else {
         e = launch_fuse(s, rows_per_item(), 0, cs);
     }

@@ -234,6 +234,9 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
     int *sums = reinterpret_cast<int *>(rep + L::kRep);
     float *qs = reinterpret_cast<float *>(sums + L::kSums);
     long long *se64 = reinterpret_cast<long long *>(wb + L::kWords * 4);
+    // Let a programmatic dependent (the MS-resolution pass) be scheduled as
+    // this grid drains (no-op without one).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (blockIdx.x == 0 && threadIdx.x == 0) *ctas_out = (int)gridDim.x;  // partial rows, for the finalize
     for (int k = 0; k < L::NS; ++k) sums[k * 32 + lane] = 0;
     for (int k = lane; k < L::kQ; k += 32) qs[k] = 0.f;

@@ -49,7 +49,8 @@ struct MetricLaunch {
     double *result;     // device pointer for the 4 results, or nullptr
     int32_t pan_done;   // PAN-resolution partial rows already written (fused forward + metrics),
                         // their count at kMetricPanCtasSlot
-    int32_t pad_;
+    int32_t ms_early;   // the kernel just before on the stream is one of ours that writes none of
+                        // the MS pass's inputs: the MS pass may start as it drains (see launch_metrics)
 };
 
 // Fused forward + PAN-resolution metrics (fuse_metrics.cu): uint8 inputs, a

@@ -277,6 +277,12 @@ metrics_pan_kernel(const __grid_constant__ MetricArgs a) {
 
 // --------------------------------------------------------------- 8-bit fast paths
 
+// Programmatic dependent launch (sm_90+): a primary lets its dependent be
+// scheduled; a dependent waits for its primary grid's completion and memory.
+// Both are no-ops without the launch attribute.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_primary() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Asynchronous global -> shared copy of one 16-byte chunk; bytes past
 // `valid` are zero-filled (the source is not read there).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned valid) {
@@ -423,6 +429,7 @@ struct FastPan {
 template <int NB, bool GEN>
 __global__ void __launch_bounds__(FastPan<NB>::kWarps * 32, 1)
 metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
+    allow_dependents();
     using C = FastPan<NB>;
     constexpr int kFastWarps = C::kWarps;
     constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
@@ -833,6 +840,7 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
         }
         out[k] = acc;
     }
+    wait_primary();  // a programmatic dependent completes only after its primary grid
 }
 
 // --------------------------------------------------------------- MS-resolution pass
@@ -1131,6 +1139,8 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     }
     if (e != cudaSuccess) return e;
     // MS-resolution pass
+    MetricLaunch ml = m;
+    if (!m.pan_done) ml.ms_early = 1;  // right after our own PAN-resolution pass
     MetricArgs b = a;
     b.partial = ms_part;
     void *args2[] = {&b};
@@ -1139,7 +1149,23 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
         const int64_t items = ((m.W / 2 + kStrip - 1) / kStrip) * ((m.H / 2 + kWin - 1) / kWin);
         e = fast_grid(fm, items, &gm);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernel(fm.fn, dim3(gm), dim3(fm.warps * 32), args2, fm.smem, stream);
+        // The MS pass reads only MS and PAN.  When the kernel before it on the
+    // stream is the PAN-resolution pass or the fused forward + metrics kernel
+    // (ms_early), it is launched as that kernel's programmatic dependent: its
+    // CTAs start on SMs the primary has drained (the primary's last wave
+    // leaves SMs idle), and it waits for the primary grid only before it
+    // exits, so work after it still sees the primary's results.
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(gm);
+        cfg.blockDim = dim3(fm.warps * 32);
+        cfg.dynamicSmemBytes = (size_t)fm.smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = ml.ms_early ? 1 : 0;
+        e = cudaLaunchKernelExC(&cfg, fm.fn, args2);
     } else {
         const void *fm = m.in_f32 ? ms_fn_nb<float>(m.bands) : ms_fn_nb<uint8_t>(m.bands);
         const int64_t items = ((m.W / 2 + kWarpCols - 1) / kWarpCols) * ((m.H / 2 + kWin - 1) / kWin);
