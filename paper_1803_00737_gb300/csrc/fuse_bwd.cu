@@ -34,6 +34,8 @@ struct BwdArgs {
     float kappa;                  // gain * sigma^2
     int32_t a4;                   // 4-pixel vector path for g / gpan
     int32_t ms2;                  // W/2 even and every gms 8-byte aligned: pair stores
+    int32_t alt;                  // W % 4 == 2 with 16-byte aligned g / gpan: shifted odd rows
+    int32_t pad_;
 };
 
 __device__ __forceinline__ void store_gms(float *row, const LaneCols &c, bool pair, float a, float b) {
@@ -69,27 +71,82 @@ __device__ __forceinline__ void store_gpan(float *p, bool a4, bool two, bool acc
     }
 }
 
-template <int NB>
+// grad_P pixels (y, x..x+3) of a row that starts 2 pixels past a 16-byte
+// boundary (W = 2 mod 4, odd rows): every lane but the first writes (or adds
+// to) the aligned vector x-2..x+1 with its left neighbour's last two values;
+// lane 0 writes x, x+1 and the last lane of the strip also x+2, x+3.  Every
+// lane of the warp must call it (warp shuffles); `active` masks the stores.
+__device__ __forceinline__ void store_gpan_shifted(float *p, int lane, bool active, bool two, bool last,
+                                                   bool acc, const float *v) {
+    const float l2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+    const float l3 = __shfl_up_sync(0xffffffffu, v[3], 1);
+    if (!active) return;
+    if (lane > 0) {
+        float4 w = make_float4(l2, l3, v[0], v[1]);
+        if (acc) {
+            const float4 o = *reinterpret_cast<const float4 *>(p - 2);
+            w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+        }
+        *reinterpret_cast<float4 *>(p - 2) = w;
+    } else {
+        float2 w = make_float2(v[0], v[1]);
+        if (acc) {
+            const float2 o = *reinterpret_cast<const float2 *>(p);
+            w.x += o.x; w.y += o.y;
+        }
+        *reinterpret_cast<float2 *>(p) = w;
+    }
+    if (two && last) {
+        float2 w = make_float2(v[2], v[3]);
+        if (acc) {
+            const float2 o = *reinterpret_cast<const float2 *>(p + 2);
+            w.x += o.x; w.y += o.y;
+        }
+        *reinterpret_cast<float2 *>(p + 2) = w;
+    }
+}
+
+// Rows 2m, 2m+1 of grad_P.  ALT: the W % 4 == 2 instance (even rows as
+// vectors but for the lane at x = W-2, odd rows shifted; all lanes call).
+template <bool ALT>
+__device__ __forceinline__ void store_gpan_rows(const BwdArgs &s, const LaneCols &c, int lane, int64_t m, bool acc,
+                                                const float *o0, const float *o1) {
+    float *r0 = s.gpan + (2 * m) * s.W + c.x, *r1 = r0 + s.W;
+    if constexpr (ALT) {
+        if (s.alt) {
+            if (c.active) store_gpan(r0, c.two, c.two, acc, o0);
+            store_gpan_shifted(r1, lane, c.active, c.two, c.last, acc, o1);
+            return;
+        }
+    }
+    if (c.active) {
+        store_gpan(r0, s.a4 != 0, c.two, acc, o0);
+        store_gpan(r1, s.a4 != 0, c.two, acc, o1);
+    }
+}
+
+template <int NB, bool ALT>
 __device__ __forceinline__ void haar_bwd_item(const BwdArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
                                               int b0, bool acc, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0, pair = s.ms2 != 0;
+    const bool lde = a4 || (ALT && s.alt != 0 && c.two);  // 4-pixel loads on even rows
     for (int64_t m = m_s; m < m_e; ++m) {
         float p0[NB][4], p1[NB][4];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float *gb = s.g + (int64_t)(b0 + b) * HW;
-            load_row4(gb + (2 * m) * W, c, a4, p0[b]);
+            load_row4(gb + (2 * m) * W, c, lde, p0[b]);
             load_row4(gb + (2 * m + 1) * W, c, a4, p1[b]);
         }
-        if (!c.active) continue;
+        if (!ALT && !c.active) continue;
         float g0[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float sA = (p0[b][0] + p0[b][1]) + (p1[b][0] + p1[b][1]);
             const float sB = (p0[b][2] + p0[b][3]) + (p1[b][2] + p1[b][3]);
-            store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
+            if (c.active) store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 g0[q] += p0[b][q];
@@ -100,8 +157,7 @@ __device__ __forceinline__ void haar_bwd_item(const BwdArgs &s, int64_t x0, int6
         const float mB = ((g0[2] + g0[3]) + (g1[2] + g1[3])) * 0.25f;
         const float v0[4] = {g0[0] - mA, g0[1] - mA, g0[2] - mB, g0[3] - mB};
         const float v1[4] = {g1[0] - mA, g1[1] - mA, g1[2] - mB, g1[3] - mB};
-        store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, acc, v0);
-        store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, acc, v1);
+        store_gpan_rows<ALT>(s, c, lane, m, acc, v0, v1);
     }
 }
 
@@ -111,12 +167,13 @@ __device__ __forceinline__ void d4_rowpass2(const float *v, float *r) {
     r[1] = fmaf(kH3, v[7], fmaf(kH2, v[6], fmaf(kH1, v[5], kH0 * v[4])));
 }
 
-template <int NB>
+template <int NB, bool ALT>
 __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
                                             int b0, bool acc, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
     const LaneCols c = lane_cols(x0, lane, W);
     const bool a4 = s.a4 != 0, pair = s.ms2 != 0;
+    const bool lde = a4 || (ALT && s.alt != 0 && c.two);  // 4-pixel loads on even rows
     const float *g = s.g + (int64_t)b0 * HW;
 
     // Prologue: PAN rows 2mp .. 2mp+3 of every band, mp = m_s - 1 (periodic).
@@ -139,7 +196,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     float v[8];
-                    load_row8(g + (int64_t)b * HW + wrap(2 * mp + r, H) * W, c, a4, v);
+                    load_row8(g + (int64_t)b * HW + wrap(2 * mp + r, H) * W, c, r == 0 ? lde : a4, v);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) ga[r][k] += v[k];
                 }
@@ -158,7 +215,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 float v[8];
-                load_row8(g + (int64_t)b * HW + wrap(2 * mp + 2 + r, H) * W, c, a4, v);
+                load_row8(g + (int64_t)b * HW + wrap(2 * mp + 2 + r, H) * W, c, r == 0 ? lde : a4, v);
 #pragma unroll
                 for (int k = 0; k < 8; ++k) ga[r][k] += v[k];
                 d4_rowpass2(v, rb[b][r]);
@@ -186,7 +243,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const float *gb = g + (int64_t)b * HW;
-            load_row8(gb + wrap(2 * m + 2, H) * W, c, a4, v[b][0]);
+            load_row8(gb + wrap(2 * m + 2, H) * W, c, lde, v[b][0]);
             load_row8(gb + wrap(2 * m + 3, H) * W, c, a4, v[b][1]);
         }
         float ga[2][8];
@@ -228,10 +285,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
             o1[q] = go1[q] - fmaf(kH3, hprev[q], kH1 * hc[q]);
             hprev[q] = hc[q];
         }
-        if (c.active) {
-            store_gpan(s.gpan + (2 * m) * W + c.x, a4, c.two, acc, o0);
-            store_gpan(s.gpan + (2 * m + 1) * W + c.x, a4, c.two, acc, o1);
-        }
+        store_gpan_rows<ALT>(s, c, lane, m, acc, o0, o1);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             rg0[k] = rn0[k];
@@ -245,7 +299,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
     }
 }
 
-template <int WAV, int NB>
+template <int WAV, int NB, bool ALT>
 __global__ void __launch_bounds__(kBwdThreads, 2)
 fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t strips_x, int64_t items, int R) {
     const int lane = threadIdx.x & 31;
@@ -255,24 +309,27 @@ fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t stri
         const int64_t m_s = sy * R;
         const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
         if (WAV == 0)
-            haar_bwd_item<NB>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
+            haar_bwd_item<NB, ALT>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
         else
-            d4_bwd_item<NB>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
+            d4_bwd_item<NB, ALT>(s, sx * kWarpCols, m_s, m_e, b0, acc != 0, lane);
     }
 }
 
 namespace {
 
 template <int WAV, int NB>
-const void *bwd_fn() { return reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB>); }
+const void *bwd_fn(bool alt) {
+    return alt ? reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, true>)
+               : reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
+}
 
 template <int WAV>
-const void *bwd_fn_nb(int nb) {
+const void *bwd_fn_nb(int nb, bool alt) {
     switch (nb) {
-        case 1: return bwd_fn<WAV, 1>();
-        case 2: return bwd_fn<WAV, 2>();
-        case 3: return bwd_fn<WAV, 3>();
-        default: return bwd_fn<WAV, 4>();
+        case 1: return bwd_fn<WAV, 1>(alt);
+        case 2: return bwd_fn<WAV, 2>(alt);
+        case 3: return bwd_fn<WAV, 3>(alt);
+        default: return bwd_fn<WAV, 4>(alt);
     }
 }
 
@@ -292,15 +349,16 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     s.W = W;
     s.bands = bands;
     s.kappa = wavelet == 0 ? 4.0f : 2.0f;  // gain * sigma^2: 1 * 4 (Haar), 2 * 1 (D4)
-    s.a4 = (W % 4 == 0) && (reinterpret_cast<uintptr_t>(g) % 16 == 0) &&
-           (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
+    const bool al16 = (reinterpret_cast<uintptr_t>(g) % 16 == 0) && (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
+    s.a4 = (W % 4 == 0) && al16;
+    s.alt = (W % 4 == 2) && al16;
     s.ms2 = ms2;
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
     for (int b0 = 0; b0 < bands; b0 += kBwdChunk) {
         const int nb = bands - b0 < kBwdChunk ? bands - b0 : kBwdChunk;
-        const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb) : bwd_fn_nb<1>(nb);
+        const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb, s.alt != 0) : bwd_fn_nb<1>(nb, s.alt != 0);
         int occ = 0;
         e = resident_blocks(fn, kBwdThreads, &occ);
         if (e != cudaSuccess) return e;
