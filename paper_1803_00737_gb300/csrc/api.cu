@@ -141,6 +141,51 @@ int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int
     return DWTFUSE_OK;
 }
 
+// Scene table of a batched launch.  A scene whose rows are 2 pixels off the
+// 16-byte grid on every other row (W % 4 == 2, aligned planes) is run by the
+// shifted-row item body, which holds at most kBatchAltMaxBands bands: with
+// more, its bands are split over two table entries (the same PAN read twice)
+// while the table has room, else it takes the plain pixel-pair body.
+int build_batch_table(const dwtfuse_scene *scenes, int n, int rows_per_item, BatchTable *t) {
+    std::memset(t, 0, sizeof *t);
+    t->R = rows_per_item > 0 ? rows_per_item : kDefaultRows;
+    int64_t acc = 0;
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        const dwtfuse_scene &d = scenes[i];
+        if (d.reserved != 0) return DWTFUSE_EINVAL;
+        SceneArgs sa;
+        const int st = make_scene(d.pan, d.ms, d.bands, d.H, d.W, d.wavelet, d.in_dtype, d.out_f32, d.out_u8,
+                                  kBatchMaxBands, &sa);
+        if (st != DWTFUSE_OK) return st;
+        const ItemGrid g = item_grid(d.H, d.W, t->R);
+        const bool alt = sa.alt && !sa.a4;
+        const bool split = alt && sa.bands > kBatchAltMaxBands && (n - i - 1) + k + 2 <= kMaxScenes;
+        if (alt && sa.bands > kBatchAltMaxBands && !split) sa.alt = 0;
+        const int parts = split ? 2 : 1;
+        const int64_t HW = d.H * d.W;
+        for (int p = 0; p < parts; ++p) {
+            SceneArgs e = sa;
+            if (split) {
+                const int b0 = p == 0 ? 0 : (sa.bands + 1) / 2;
+                const int nb = p == 0 ? (sa.bands + 1) / 2 : sa.bands - (sa.bands + 1) / 2;
+                for (int b = 0; b < kMaxBands; ++b) e.ms[b] = b < nb ? sa.ms[b0 + b] : nullptr;
+                e.bands = nb;
+                if (e.out_f32) e.out_f32 += (int64_t)b0 * HW;
+                if (e.out_u8) e.out_u8 += (int64_t)b0 * HW;
+            }
+            t->scenes[k] = e;
+            t->item_start[k] = acc;
+            t->strips_x[k] = g.strips_x;
+            acc += g.items;
+            ++k;
+        }
+    }
+    t->n = k;
+    t->item_start[k] = acc;
+    return DWTFUSE_OK;
+}
+
 }  // namespace dwtfuse
 
 using namespace dwtfuse;
@@ -421,22 +466,8 @@ int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, si
     if (ws_bytes < dwtfuse_batched_workspace_size()) return DWTFUSE_ENOMEM;
     if (!aligned(workspace, 16)) return DWTFUSE_EALIGN;
     static thread_local BatchTable t;  // ~27 KB: kept off the stack
-    std::memset(&t, 0, sizeof t);
-    t.n = n;
-    t.R = rows_per_item_ > 0 ? rows_per_item_ : kDefaultRows;
-    int64_t acc = 0;
-    for (int i = 0; i < n; ++i) {
-        const dwtfuse_scene &d = scenes[i];
-        if (d.reserved != 0) return DWTFUSE_EINVAL;
-        const int st = make_scene(d.pan, d.ms, d.bands, d.H, d.W, d.wavelet, d.in_dtype, d.out_f32,
-                                  d.out_u8, kBatchMaxBands, &t.scenes[i]);
-        if (st != DWTFUSE_OK) return st;
-        const ItemGrid g = item_grid(d.H, d.W, t.R);
-        t.item_start[i] = acc;
-        t.strips_x[i] = g.strips_x;
-        acc += g.items;
-    }
-    t.item_start[n] = acc;
+    const int st = build_batch_table(scenes, n, rows_per_item_, &t);
+    if (st != DWTFUSE_OK) return st;
     auto *queue = static_cast<unsigned long long *>(workspace);
     int *status = reinterpret_cast<int *>(static_cast<char *>(workspace) + 8);
     return cuda_status(launch_fuse_batched(t, queue, status, blocks_per_sm, static_cast<cudaStream_t>(stream)));

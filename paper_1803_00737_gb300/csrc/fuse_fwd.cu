@@ -50,6 +50,18 @@ fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *qu
         const int nb = s.bands;
 #define DWTFUSE_CASE(NBV)                                                                    \
     case NBV:                                                                                \
+        if constexpr (NBV <= kBatchAltMaxBands) {                                            \
+            if (s.alt && !s.a4) {                                                            \
+                if (s.in_f32) {                                                              \
+                    if (s.wavelet) run_item<float, 1, NBV, true>(s, local, sx, t.R, 0, NBV, lane);   \
+                    else run_item<float, 0, NBV, true>(s, local, sx, t.R, 0, NBV, lane);             \
+                } else {                                                                     \
+                    if (s.wavelet) run_item<uint8_t, 1, NBV, true>(s, local, sx, t.R, 0, NBV, lane); \
+                    else run_item<uint8_t, 0, NBV, true>(s, local, sx, t.R, 0, NBV, lane);           \
+                }                                                                            \
+                break;                                                                       \
+            }                                                                                \
+        }                                                                                    \
         if (s.in_f32) {                                                                      \
             if (s.wavelet) run_item<float, 1, NBV>(s, local, sx, t.R, 0, NBV, lane);         \
             else run_item<float, 0, NBV>(s, local, sx, t.R, 0, NBV, lane);                   \

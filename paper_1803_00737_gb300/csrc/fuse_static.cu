@@ -15,9 +15,7 @@
 namespace dwtfuse {
 
 // Defined in api.cu.
-int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
-               int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, int max_bands,
-               SceneArgs *s);
+int build_batch_table(const dwtfuse_scene *scenes, int n, int rows_per_item, BatchTable *t);
 int cuda_status(cudaError_t e);
 
 namespace {
@@ -60,24 +58,10 @@ extern "C" int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, 
     if (n > kMaxScenes) return DWTFUSE_ESHAPE;
     if (kQueueBytes > DWTFUSE_STATIC_SCRATCH_BYTES) return DWTFUSE_ENOMEM;
     static thread_local BatchTable t;
-    std::memset(&t, 0, sizeof t);
-    t.n = n;
-    t.R = rows_per_item > 0 ? rows_per_item : kDefaultRows;
-    int64_t acc = 0;
-    for (int i = 0; i < n; ++i) {
-        const dwtfuse_scene &d = scenes[i];
-        if (d.reserved != 0) return DWTFUSE_EINVAL;
-        const int st = make_scene(d.pan, d.ms, d.bands, d.H, d.W, d.wavelet, d.in_dtype, d.out_f32,
-                                  d.out_u8, kBatchMaxBands, &t.scenes[i]);
-        if (st != DWTFUSE_OK) return st;
-        const ItemGrid g = item_grid(d.H, d.W, t.R);
-        t.item_start[i] = acc;
-        t.strips_x[i] = g.strips_x;
-        acc += g.items;
-    }
-    t.item_start[n] = acc;
+    int st = build_batch_table(scenes, n, rows_per_item, &t);
+    if (st != DWTFUSE_OK) return st;
     void *scratch = nullptr;
-    const int st = scratch_address(&scratch);
+    st = scratch_address(&scratch);
     if (st != DWTFUSE_OK) return st;
     // launch_fuse_batched clears the counter and status word before the kernel.
     auto *queue = static_cast<unsigned long long *>(scratch);

@@ -9,7 +9,8 @@
 namespace dwtfuse {
 
 constexpr int kChunkBands = 8;     // bands per single-scene launch (more = several launches)
-constexpr int kBatchMaxBands = 8;  // bands per scene in the batched kernel
+constexpr int kBatchMaxBands = 8;
+constexpr int kBatchAltMaxBands = 6;  // bands of the batched shifted-row (W % 4 == 2) item body  // bands per scene in the batched kernel
 constexpr int kMaxScenes = 128;    // scenes per batched launch
 constexpr int kDefaultRows = 32;   // MS rows per warp work item (batched default)
 constexpr size_t kQueueBytes = 16; // queue counter (8) + status word (4) + pad
