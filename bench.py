@@ -65,8 +65,8 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, vendor figure (context; the measured co
 # sources it was taken on.
 KNOWN_TRAFFIC: dict[str, float] = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
-    # read 689,733,376 + write 7,991,625,984 (profiles/fuse_metrics_d4_4096x4096_b6.md)
-    "4230335fb78f": 8681359360.0,
+    # read 689,832,448 + write 7,991,618,304 (profiles/fuse_metrics_d4_4096x4096_b6.md)
+    "88490acee432": 8681450752.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
