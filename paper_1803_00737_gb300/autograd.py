@@ -12,6 +12,22 @@ import torch
 from . import _C
 
 
+def fuse_batch(P: torch.Tensor, M: torch.Tensor, wavelet: int, out: torch.Tensor) -> None:
+    """Float forward of a batch: P (N, H, W), M (N, B, H/2, W/2), out (N, B, H, W).
+    Batches go through the batched persistent kernel (one launch per up to
+    DWTFUSE_MAX_SCENES scenes, its workspace from torch's allocator); a single
+    scene, or more than 8 bands, through dwtfuse_fuse."""
+    N, B = M.shape[0], M.shape[1]
+    if N == 1 or B > 8:
+        for i in range(N):
+            _C.dwtfuse_fuse(P[i], M[i], wavelet, out[i], None)
+        return
+    ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=P.device)
+    for i0 in range(0, N, _C.MAX_SCENES):
+        scenes = [_C.make_scene(P[i], M[i], wavelet, out[i], None) for i in range(i0, min(N, i0 + _C.MAX_SCENES))]
+        _C.dwtfuse_fuse_batched(scenes, ws)
+
+
 class DWTFuseFn(torch.autograd.Function):
     """fused = DWTFuseFn.apply(pan, ms, wavelet)
 
@@ -31,8 +47,7 @@ class DWTFuseFn(torch.autograd.Function):
         if M.shape != (N, B, H // 2, W // 2):
             raise ValueError("ms must be (N, B, H/2, W/2) matching pan (N, H, W)")
         out = torch.empty((N, B, H, W), dtype=torch.float32, device=P.device)
-        for i in range(N):
-            _C.dwtfuse_fuse(P[i], M[i], wavelet, out[i], None)
+        fuse_batch(P, M, wavelet, out)
         ctx.wavelet = int(wavelet)
         ctx.batched = batched
         ctx.shape = (N, B, H, W)
