@@ -226,6 +226,29 @@ typedef struct {
 
 #define DWTFUSE_MAX_SCENES 128
 
+/* One scene of a batched backward (all pointers on the device, as for
+ * dwtfuse_fuse_backward). */
+typedef struct {
+    const float *grad_out;             /* [bands][H][W] */
+    float *grad_pan;                   /* H x W (overwritten) */
+    float *grad_ms[DWTFUSE_MAX_BANDS]; /* bands planes (H/2) x (W/2) (overwritten) */
+    int64_t H, W;
+    int32_t bands;
+    int32_t wavelet;  /* dwtfuse_wavelet */
+} dwtfuse_grad_scene;
+
+/*
+ * Batched adjoint: dwtfuse_fuse_backward for up to DWTFUSE_MAX_SCENES scenes
+ * of any legal sizes, as one persistent launch per chunk of 4 bands (the
+ * second and later chunks add into grad_pan, so they follow in order).
+ * Arguments, layouts and errors per scene as dwtfuse_fuse_backward; the
+ * workspace is dwtfuse_batched_workspace_size() bytes of device memory, 16-byte
+ * aligned, scratch between calls (calls sharing it must not overlap).
+ * Asynchronous on `stream`; the scene array is read before the call returns.
+ */
+int dwtfuse_fuse_backward_batched(const dwtfuse_grad_scene *scenes, int n, void *workspace,
+                                  size_t ws_bytes, void *stream);
+
 /* Bytes of device workspace dwtfuse_fuse_batched needs (queue counter and
  * device status word). */
 size_t dwtfuse_batched_workspace_size(void);

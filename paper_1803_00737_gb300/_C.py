@@ -52,6 +52,19 @@ class Scene(ctypes.Structure):
     ]
 
 
+class GradScene(ctypes.Structure):
+    """dwtfuse_grad_scene of include/dwtfuse.h."""
+    _fields_ = [
+        ("grad_out", _vp),
+        ("grad_pan", _vp),
+        ("grad_ms", _vp * MAX_BANDS),
+        ("H", _i64),
+        ("W", _i64),
+        ("bands", ctypes.c_int32),
+        ("wavelet", ctypes.c_int32),
+    ]
+
+
 _SIGS = {
     "dwtfuse_status_string": (ctypes.c_char_p, [_i]),
     "dwtfuse_version": (_i, []),
@@ -62,6 +75,7 @@ _SIGS = {
     "dwtfuse_dwt2": (_i, [_vp, _i, _i64, _i64, _i, _vp, _vp]),
     "dwtfuse_idwt2": (_i, [_vp, _i64, _i64, _i, _vp, _vp, _vp]),
     "dwtfuse_fuse_backward": (_i, [_vp, _i, _i64, _i64, _i, _vp, ctypes.POINTER(_vp), _vp]),
+    "dwtfuse_fuse_backward_batched": (_i, [ctypes.POINTER(GradScene), _i, _vp, _sz, _vp]),
     "dwtfuse_batched_workspace_size": (_sz, []),
     "dwtfuse_fuse_batched": (_i, [ctypes.POINTER(Scene), _i, _vp, _sz, _i, _i, _vp]),
     "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
@@ -212,6 +226,31 @@ def dwtfuse_fuse_backward(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.
     st = lib().dwtfuse_fuse_backward(_dev(grad_out, "grad_out"), B, H, W, int(wavelet),
                                      _dev(grad_pan, "grad_pan"), ptrs, _stream(stream))
     _check(st, "dwtfuse_fuse_backward")
+
+
+def make_grad_scene(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.Tensor, grad_ms) -> GradScene:
+    B, H, W = grad_out.shape
+    if grad_out.dtype != torch.float32 or grad_pan.dtype != torch.float32:
+        raise TypeError("gradients must be float32")
+    gms = _bands(grad_ms)
+    if len(gms) != B:
+        raise ValueError("one grad_ms buffer per band")
+    s = GradScene()
+    s.grad_out = _dev(grad_out, "grad_out")
+    s.grad_pan = _dev(grad_pan, "grad_pan")
+    for b, g in enumerate(gms):
+        s.grad_ms[b] = _dev(g, f"grad_ms[{b}]")
+    s.H, s.W, s.bands, s.wavelet = H, W, B, int(wavelet)
+    return s
+
+
+def dwtfuse_fuse_backward_batched(scenes: list[GradScene], workspace: torch.Tensor, stream=None) -> None:
+    """The adjoint of every scene in one persistent launch per chunk of 4 bands."""
+    arr = (GradScene * len(scenes))(*scenes)
+    st = lib().dwtfuse_fuse_backward_batched(arr, len(scenes), _dev(workspace, "workspace"),
+                                             workspace.numel() * workspace.element_size(),
+                                             _stream(stream))
+    _check(st, "dwtfuse_fuse_backward_batched")
 
 
 def dwtfuse_batched_workspace_size() -> int:

@@ -28,6 +28,21 @@ def fuse_batch(P: torch.Tensor, M: torch.Tensor, wavelet: int, out: torch.Tensor
         _C.dwtfuse_fuse_batched(scenes, ws)
 
 
+def fuse_batch_backward(g: torch.Tensor, wavelet: int, gp: torch.Tensor, gm: torch.Tensor) -> None:
+    """Adjoint of a batch: g (N, B, H, W) into gp (N, H, W) and gm (N, B, H/2, W/2).
+    Batches go through the batched adjoint (one persistent launch per chunk of
+    4 bands over up to DWTFUSE_MAX_SCENES scenes); a single scene through
+    dwtfuse_fuse_backward."""
+    N = g.shape[0]
+    if N == 1:
+        _C.dwtfuse_fuse_backward(g[0], wavelet, gp[0], gm[0])
+        return
+    ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=g.device)
+    for i0 in range(0, N, _C.MAX_SCENES):
+        scenes = [_C.make_grad_scene(g[i], wavelet, gp[i], gm[i]) for i in range(i0, min(N, i0 + _C.MAX_SCENES))]
+        _C.dwtfuse_fuse_backward_batched(scenes, ws)
+
+
 class DWTFuseFn(torch.autograd.Function):
     """fused = DWTFuseFn.apply(pan, ms, wavelet)
 
@@ -59,8 +74,7 @@ class DWTFuseFn(torch.autograd.Function):
         g = (grad if ctx.batched else grad.unsqueeze(0)).contiguous().float()
         gp = torch.empty((N, H, W), dtype=torch.float32, device=g.device)
         gm = torch.empty((N, B, H // 2, W // 2), dtype=torch.float32, device=g.device)
-        for i in range(N):
-            _C.dwtfuse_fuse_backward(g[i], ctx.wavelet, gp[i], gm[i])
+        fuse_batch_backward(g, ctx.wavelet, gp, gm)
         if not ctx.batched:
             gp, gm = gp[0], gm[0]
         return gp, gm, None

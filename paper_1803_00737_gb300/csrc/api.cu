@@ -1,6 +1,7 @@
 // C ABI of libdwtfuse: argument validation, launch-shape selection and
 // dispatch to the kernels.  Declarations and the contract are in dwtfuse.h.
 #include <atomic>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <map>
@@ -290,6 +291,33 @@ int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W
     }
     return cuda_status(launch_fuse_backward(grad_out, bands, H, W, wavelet, grad_pan, grad_ms,
                                             rows_per_item(), static_cast<cudaStream_t>(stream)));
+}
+
+// The Python binding mirrors this layout field by field.
+static_assert(sizeof(dwtfuse_grad_scene) == 168 && offsetof(dwtfuse_grad_scene, H) == 144,
+              "dwtfuse_grad_scene layout");
+
+int dwtfuse_fuse_backward_batched(const dwtfuse_grad_scene *scenes, int n, void *workspace, size_t ws_bytes,
+                                  void *stream) {
+    if (!scenes || n < 1 || !workspace) return DWTFUSE_EINVAL;
+    if (n > kMaxScenes) return DWTFUSE_ESHAPE;
+    if (ws_bytes < dwtfuse_batched_workspace_size()) return DWTFUSE_ENOMEM;
+    if (!aligned(workspace, 16)) return DWTFUSE_EALIGN;
+    for (int i = 0; i < n; ++i) {
+        const dwtfuse_grad_scene &d = scenes[i];
+        if (!d.grad_out || !d.grad_pan) return DWTFUSE_EINVAL;
+        const int st = check_shape(d.H, d.W, d.wavelet);
+        if (st != DWTFUSE_OK) return st;
+        if (d.bands < 1) return DWTFUSE_EINVAL;
+        if (d.bands > kMaxBands) return DWTFUSE_ESHAPE;
+        if (!aligned(d.grad_out, 8) || !aligned(d.grad_pan, 8)) return DWTFUSE_EALIGN;
+        for (int b = 0; b < d.bands; ++b) {
+            if (!d.grad_ms[b]) return DWTFUSE_EINVAL;
+            if (!aligned(d.grad_ms[b], 4)) return DWTFUSE_EALIGN;
+        }
+    }
+    return cuda_status(launch_fuse_backward_batched(scenes, n, static_cast<unsigned long long *>(workspace),
+                                                    static_cast<cudaStream_t>(stream)));
 }
 
 size_t dwtfuse_metrics_workspace_size(void) { return kMetricWorkspaceBytes; }

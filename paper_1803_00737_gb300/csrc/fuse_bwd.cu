@@ -16,6 +16,8 @@
 // row low-pass of the two previous rows (a sliding vertical window), plus the
 // same for G, in registers.  Up to 4 bands per launch; further launches over
 // the remaining bands add their G - U(LL(G)) into grad_P.
+#include <cstring>
+
 #include "fuse_tile.cuh"
 #include "launch.h"
 
@@ -35,8 +37,20 @@ struct BwdArgs {
     int32_t a4;                   // 4-pixel vector path for g / gpan
     int32_t ms2;                  // W/2 even and every gms 8-byte aligned: pair stores
     int32_t alt;                  // W % 4 == 2 with 16-byte aligned g / gpan: shifted odd rows
-    int32_t pad_;
+    int32_t wavelet;              // 0 Haar, 1 D4
 };
+
+// Scene table of one launch of the batched backward (band chunk b0 of n scenes).
+struct BwdBatchTable {
+    int32_t n;
+    int32_t R;
+    int32_t b0;
+    int32_t pad_;
+    int64_t item_start[kMaxScenes + 1];
+    int64_t strips_x[kMaxScenes];
+    BwdArgs scenes[kMaxScenes];
+};
+static_assert(sizeof(BwdBatchTable) + 16 <= 32764, "batched backward table exceeds the parameter limit");
 
 __device__ __forceinline__ void store_gms(float *row, const LaneCols &c, bool pair, float a, float b) {
     if (pair) {
@@ -315,6 +329,50 @@ fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t stri
     }
 }
 
+// Batched: launch `chunk` of a batched backward covers band chunk `chunk` of
+// every scene that has one (item ranges by prefix sums, an atomic queue as in
+// the batched forward); chunks after the first add into grad_P, so they run as
+// separate launches in order.
+__global__ void __launch_bounds__(kBwdThreads, 2)
+fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long long *queue) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)t.item_start[t.n];
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        int lo = 0, hi = t.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)t.item_start[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const BwdArgs &s = t.scenes[lo];
+        const int64_t local = (int64_t)(it - (unsigned long long)t.item_start[lo]);
+        const int64_t sx = local % t.strips_x[lo], sy = local / t.strips_x[lo];
+        const int64_t m_s = sy * t.R;
+        const int64_t m_e = min(m_s + (int64_t)t.R, s.H >> 1);
+        const int b0 = t.b0, nb = min(s.bands - b0, kBwdChunk);
+        const bool acc = b0 > 0, alt = s.alt != 0;
+        const int64_t x0 = sx * kWarpCols;
+#define DWTFUSE_BWD_CASE(NBV)                                                                 \
+    case NBV:                                                                                 \
+        if (s.wavelet == 0) {                                                                 \
+            if (alt) haar_bwd_item<NBV, true>(s, x0, m_s, m_e, b0, acc, lane);                 \
+            else haar_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                    \
+        } else {                                                                              \
+            if (alt) d4_bwd_item<NBV, true>(s, x0, m_s, m_e, b0, acc, lane);                   \
+            else d4_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                      \
+        }                                                                                     \
+        break;
+        switch (nb) {
+            DWTFUSE_BWD_CASE(1) DWTFUSE_BWD_CASE(2) DWTFUSE_BWD_CASE(3) DWTFUSE_BWD_CASE(4)
+            default: break;
+        }
+#undef DWTFUSE_BWD_CASE
+    }
+}
+
 namespace {
 
 template <int WAV, int NB>
@@ -335,8 +393,8 @@ const void *bwd_fn_nb(int nb, bool alt) {
 
 }  // namespace
 
-cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
-                                 float *gpan, float *const *gms, int R, cudaStream_t stream) {
+BwdArgs make_bwd_args(const float *g, int bands, int64_t H, int64_t W, int wavelet, float *gpan,
+                      float *const *gms) {
     BwdArgs s{};
     s.g = g;
     s.gpan = gpan;
@@ -349,10 +407,63 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     s.W = W;
     s.bands = bands;
     s.kappa = wavelet == 0 ? 4.0f : 2.0f;  // gain * sigma^2: 1 * 4 (Haar), 2 * 1 (D4)
+    s.wavelet = wavelet;
     const bool al16 = (reinterpret_cast<uintptr_t>(g) % 16 == 0) && (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.a4 = (W % 4 == 0) && al16;
     s.alt = (W % 4 == 2) && al16;
     s.ms2 = ms2;
+    return s;
+}
+
+cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, unsigned long long *queue,
+                                         cudaStream_t stream) {
+    static thread_local BwdBatchTable t;  // ~28 KB: kept off the stack
+    static thread_local BwdArgs scenes[kMaxScenes];
+    int max_bands = 0;
+    for (int i = 0; i < n; ++i) {
+        scenes[i] = make_bwd_args(in[i].grad_out, in[i].bands, in[i].H, in[i].W, in[i].wavelet, in[i].grad_pan,
+                                  in[i].grad_ms);
+        max_bands = in[i].bands > max_bands ? in[i].bands : max_bands;
+    }
+    const void *fn = reinterpret_cast<const void *>(&fuse_bwd_batched_kernel);
+    int occ = 0, sms = 0;
+    cudaError_t e = resident_blocks(fn, kBwdThreads, &occ);
+    if (e != cudaSuccess) return e;
+    e = sm_count(&sms);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = (int64_t)sms * occ;
+    for (int b0 = 0; b0 < max_bands; b0 += kBwdChunk) {
+        std::memset(&t, 0, sizeof t);
+        t.R = kDefaultRows;
+        t.b0 = b0;
+        int64_t acc = 0;
+        int k = 0;
+        for (int i = 0; i < n; ++i) {
+            if (scenes[i].bands <= b0) continue;
+            const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
+            t.scenes[k] = scenes[i];
+            t.item_start[k] = acc;
+            t.strips_x[k] = g.strips_x;
+            acc += g.items;
+            ++k;
+        }
+        t.n = k;
+        t.item_start[k] = acc;
+        const int64_t need = (acc + kBwdWarps - 1) / kBwdWarps;
+        const unsigned grid = (unsigned)(need < cap ? need : cap);
+        if (grid == 0) continue;
+        e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
+        if (e != cudaSuccess) return e;
+        fuse_bwd_batched_kernel<<<grid, kBwdThreads, 0, stream>>>(t, queue);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
+                                 float *gpan, float *const *gms, int R, cudaStream_t stream) {
+    BwdArgs s = make_bwd_args(g, bands, H, W, wavelet, gpan, gms);
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;

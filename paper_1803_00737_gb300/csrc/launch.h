@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dwtfuse.h"
 #include "fuse_tile.cuh"
 
 namespace dwtfuse {
@@ -100,6 +101,9 @@ cudaError_t resident_blocks_smem(const void *fn, int threads, int smem, int *out
 cudaError_t sm_count(int *out);
 
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream);
+// Batched adjoint over validated scenes (fuse_bwd.cu).
+cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *scenes, int n, unsigned long long *queue,
+                                         cudaStream_t stream);
 cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W, int wavelet,
                                  float *gpan, float *const *gms, int R, cudaStream_t stream);
 cudaError_t launch_dwt2(const DwtLaunch &d, cudaStream_t stream);

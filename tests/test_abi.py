@@ -114,6 +114,37 @@ def test_batched_validation(L):
     assert L.dwtfuse_fuse_batched(arr, 1, FAKE, ws, 0, 0, None) == _C.EINVAL
 
 
+def test_batched_backward_validation(L):
+    s = _C.GradScene()
+    s.grad_out, s.grad_pan = FAKE, FAKE
+    s.grad_ms[0] = s.grad_ms[1] = FAKE
+    s.H, s.W, s.bands, s.wavelet = 4, 4, 2, 1
+    ws = _C.lib().dwtfuse_batched_workspace_size()
+
+    def call(n=1, w=FAKE, nbytes=ws):
+        return L.dwtfuse_fuse_backward_batched((_C.GradScene * 1)(s), n, w, nbytes, None)
+
+    assert call(n=0) == _C.EINVAL
+    assert call(n=129) == _C.ESHAPE
+    assert call(w=None) == _C.EINVAL
+    assert call(nbytes=ws - 1) == _C.ENOMEM
+    assert call(w=FAKE + 8) == _C.EALIGN
+    s.W = 5
+    assert call() == _C.ESHAPE
+    s.W, s.bands = 4, 17
+    assert call() == _C.ESHAPE
+    s.bands = 0
+    assert call() == _C.EINVAL
+    s.bands, s.wavelet = 2, 2
+    assert call() == _C.EINVAL
+    s.wavelet, s.grad_out = 1, FAKE + 4
+    assert call() == _C.EALIGN
+    s.grad_out, s.grad_ms[1] = FAKE, None
+    assert call() == _C.EINVAL
+    s.grad_ms[1] = FAKE + 2
+    assert call() == _C.EALIGN
+
+
 def test_rows_knob(L):
     assert L.dwtfuse_set_rows_per_item(-1) == _C.EINVAL
     assert L.dwtfuse_set_rows_per_item(16) == _C.OK

@@ -99,10 +99,11 @@ def test_gradients_vs_fp64_finite_differences_64(wav):
 
 
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
-def test_autograd_mse_loss(wav):
-    """Batch of 2 D4/Haar scenes as float32; loss = MSE to a seeded target; the
-    gradients equal the oracle adjoint of 2 (F - T) / numel."""
-    N, B, H, W = 2, 4, 64, 96
+@pytest.mark.parametrize("N,B,H,W", [(2, 4, 64, 96), (3, 9, 66, 130)])
+def test_autograd_mse_loss(wav, N, B, H, W):
+    """Batches of D4/Haar scenes as float32 (the second: 9 bands, three band
+    chunks in the batched adjoint, W = 2 mod 4); loss = MSE to a seeded target;
+    the gradients equal the oracle adjoint of 2 (F - T) / numel."""
     pans, mss = [], []
     for i in range(N):
         p, m = scenegen.make_scene(H, W, B, seed=i)
@@ -151,3 +152,74 @@ def test_dot_product_identity_config3_size():
     lhs = (out.double() * y.double()).sum().item()
     rhs = (pan.double() * gp.double()).sum().item() + (ms.double() * gm.double()).sum().item()
     assert abs(lhs - rhs) <= 1e-5 * (out.double().abs() * y.double().abs()).sum().item()
+
+
+# Mixed batch: both wavelets, W = 0 and 2 mod 4 and off the 128-column strip
+# grid, odd H/2, 1 to 16 bands (one to four band chunks; scenes with fewer
+# bands drop out of the later chunks).
+BATCH = [((64, 64), 3, O.D4), ((66, 258), 4, O.HAAR), ((130, 250), 9, O.D4), ((12, 814), 1, O.HAAR),
+         ((4, 4), 2, O.D4), ((200, 136), 6, O.HAAR), ((98, 610), 5, O.D4), ((256, 512), 16, O.D4),
+         ((6, 18), 13, O.HAAR), ((1030, 196), 8, O.D4)]
+
+
+def _batch(specs, seed):
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(seed)
+    rows = []
+    for (H, W), B, wav in specs:
+        g = torch.randn((B, H, W), generator=gen, device=DEV)
+        gp = torch.full((H, W), float("nan"), device=DEV)
+        gm = torch.full((B, H // 2, W // 2), float("nan"), device=DEV)
+        rows.append((g, wav, gp, gm))
+    return rows
+
+
+def _per_scene(rows):
+    refs = []
+    for g, wav, gp, gm in rows:
+        rp, rm = torch.empty_like(gp), torch.empty_like(gm)
+        _C.dwtfuse_fuse_backward(g, wav, rp, rm)
+        refs.append((rp, rm))
+    return refs
+
+
+def test_batched_backward_equals_per_scene():
+    """dwtfuse_fuse_backward_batched gives the per-scene adjoint's bits: the
+    same item arithmetic, band chunks in the same order."""
+    rows = _batch(BATCH, 7)
+    ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_fuse_backward_batched([_C.make_grad_scene(*r) for r in rows], ws)
+    refs = _per_scene(rows)
+    torch.cuda.synchronize()
+    for (g, wav, gp, gm), (rp, rm) in zip(rows, refs):
+        assert torch.equal(gp, rp) and torch.equal(gm, rm), (tuple(g.shape), wav)
+
+
+def test_batched_backward_against_oracle():
+    rows = _batch(BATCH[:4], 8)
+    ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_fuse_backward_batched([_C.make_grad_scene(*r) for r in rows], ws)
+    torch.cuda.synchronize()
+    for g, wav, gp, gm in rows:
+        rp, rm = O.fuse_adjoint(g.cpu().numpy().astype(np.float64), wav)
+        assert_close(gp.cpu().numpy().astype(np.float64), rp)
+        assert_close(gm.cpu().numpy().astype(np.float64), rm)
+
+
+def test_batched_backward_full_table_and_graph():
+    """128 scenes (the table's capacity) captured in a CUDA graph and replayed."""
+    specs = [((8 + 4 * (i % 9), 6 + 4 * (i % 11)), 1 + i % 6, O.D4 if i % 3 else O.HAAR) for i in range(128)]
+    rows = _batch(specs, 9)
+    ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=DEV)
+    scenes = [_C.make_grad_scene(*r) for r in rows]
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            _C.dwtfuse_fuse_backward_batched(scenes, ws, stream=s)
+    graph.replay()
+    refs = _per_scene(rows)
+    torch.cuda.synchronize()
+    for (g, wav, gp, gm), (rp, rm) in zip(rows, refs):
+        assert torch.equal(gp, rp) and torch.equal(gm, rm), (tuple(g.shape), wav)

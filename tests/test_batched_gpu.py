@@ -117,3 +117,24 @@ def test_batched_uneven_config_full_size():
         ref = O.fuse_points(pan_h, ms[b].cpu().numpy(), sp.wavelet, ys, xs)
         got = out[b][yt, xt].cpu().numpy().astype(np.float64)
         assert np.abs(got - ref).max() <= (0 if sp.wavelet == O.HAAR else 5e-4), sp
+
+
+def test_batched_band_groups_and_table_capacity():
+    """Scenes with W = 2 mod 4 and 7-8 bands run as two band groups (two
+    table entries) while the table has room; at DWTFUSE_MAX_SCENES such
+    scenes, the ones that no longer fit take the pixel-pair body.  Results
+    equal the single-scene path either way."""
+    specs = [scenegen.SceneSpec(6 + 2 * (i % 5), 10 + 4 * (i % 7), 7 + (i % 2), O.D4 if i % 3 else O.HAAR, 100 + i)
+             for i in range(_C.MAX_SCENES)]
+    assert all(sp.W % 4 == 2 for sp in specs)
+    for n in (3, _C.MAX_SCENES):
+        scenes, keep = _make(specs[:n])
+        ws = _workspace()
+        _C.dwtfuse_fuse_batched(scenes, ws)
+        torch.cuda.synchronize()
+        assert _C.dwtfuse_get_last_device_status(ws) == _C.OK
+        for sp, pan, ms, out, out8 in keep:
+            f, u = fuse(pan, ms, sp.wavelet, f32=True, u8=True)
+            torch.cuda.synchronize()
+            assert torch.equal(out, f), sp
+            assert torch.equal(out8, u), sp
