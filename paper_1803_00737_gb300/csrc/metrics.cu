@@ -297,46 +297,121 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Copies the bytes [a0, a0 + span) of one image row into shared memory as
-// 16-byte chunks starting at the aligned address floor16(a0), so the row's
-// byte i lands at dst[(a0 & 15) + i].  Chunks are spread over the lanes.
-// Bytes outside the image plane [lo, hi) are never read: a chunk crossing
-// hi is zero-filled past it; a chunk starting before lo (a plane that is
-// not 16-byte aligned) is copied byte by byte.
-// Plane edges (out of line: rare, and inlined at every row copy it would
-// crowd the instruction cache).
-static __device__ __noinline__ void copy_row_edge(unsigned char *dst, const uint8_t *c0, int nchunks,
-                                                  const uint8_t *lo, const uint8_t *hi, int lane) {
-    for (int k = lane; k < nchunks; k += 32) {
-        const uint8_t *src = c0 + 16 * k;
-        if (src >= hi || src + 16 <= lo) continue;
-        if (src >= lo) {
-            const int64_t v = hi - src;
-            cp_async16(dst + 16 * k, src, v >= 16 ? 16u : (unsigned)v);
-        } else {
-            for (int i = 0; i < 16; ++i)
-                if (src + i >= lo && src + i < hi) dst[16 * k + i] = __ldg(src + i);
-        }
+// Rows of unaligned planes (any width, any plane alignment) are staged with
+// the bulk copy engine: the lane that owns a plane copies the 16-byte chunks of
+// its row segment that lie inside the plane with one cp.async.bulk, which
+// completes on the ring slot's mbarrier, so byte i of the segment lands at
+// dst[(a0 & 15) + i].  The at most 15 bytes at either plane end that no
+// in-plane chunk covers are copied with plain loads (bytes outside the plane
+// are never read).
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits (the whole warp) for the phase of `bar` with parity `parity`; gives up
+// after about a second (the copies of one row take microseconds) and returns
+// false, the same answer on every lane.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, unsigned parity) {
+    bool done = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (!done) done = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        unsigned late = global_ns() - t0 > 1000000000ull;
+        if (__any_sync(0xffffffffu, late)) return false;
+    }
+}
+static __device__ __noinline__ void stage_bytes(unsigned char *dst, uintptr_t c0, uintptr_t from, uintptr_t to) {
+    for (uintptr_t p = from; p < to; ++p) dst[p - c0] = __ldg(reinterpret_cast<const uint8_t *>(p));
+}
+__device__ __forceinline__ void stage_row(unsigned char *dst, const uint8_t *a0, int len, const uint8_t *lo,
+                                          const uint8_t *hi, uint64_t *bar) {
+    const uintptr_t ua = reinterpret_cast<uintptr_t>(a0), c0 = ua & ~(uintptr_t)15, ue = ua + (uintptr_t)len;
+    const uintptr_t ulo = reinterpret_cast<uintptr_t>(lo), uhi = reinterpret_cast<uintptr_t>(hi);
+    uintptr_t bs = c0, be = (ue + 15) & ~(uintptr_t)15;
+    if (bs < ulo) bs = (ulo + 15) & ~(uintptr_t)15;
+    if (be > uhi) be = uhi & ~(uintptr_t)15;
+    if (be > bs) {
+        const unsigned n = (unsigned)(be - bs);
+        mbar_expect_tx(bar, n);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                         smem_u32(dst + (bs - c0))),
+                     "l"(reinterpret_cast<const void *>(bs)), "r"(n), "r"(smem_u32(bar))
+                     : "memory");
+        if (ua < bs) stage_bytes(dst, c0, ua, bs);
+        if (be < ue) stage_bytes(dst, c0, be, ue);
+    } else {
+        stage_bytes(dst, c0, ua, ue);
     }
 }
 
-template <int MAXCH>  // most chunks a row can have (a bound known at compile time)
-__device__ __forceinline__ void copy_row(unsigned char *dst, const uint8_t *a0, int span,
-                                         const uint8_t *lo, const uint8_t *hi, int lane) {
-    const uintptr_t ua = reinterpret_cast<uintptr_t>(a0);
-    const uint8_t *c0 = reinterpret_cast<const uint8_t *>(ua & ~(uintptr_t)15);
-    const int nchunks = ((int)(ua & 15) + span + 15) >> 4;
-    if (c0 >= lo && c0 + 16 * nchunks <= hi) {
-        // the whole span lies inside the plane (every row but a plane's first or last)
-#pragma unroll
-        for (int t = 0; t < (MAXCH + 31) / 32; ++t) {
-            const int k = lane + 32 * t;
-            if (k < nchunks) cp_async16(dst + 16 * k, c0 + 16 * k, 16u);
-        }
-        return;
+// Per-warp ring of row slots for the unaligned path: slot k's mbarrier
+// completes when every bulk copy of the row staged there has landed (the one
+// arrival is lane 0's, after all lanes have posted their byte counts).
+template <int S>
+struct BulkRing {
+    uint64_t *bar;
+    unsigned phase = 0;  // bit k: parity of slot k's next phase
+    int issue_slot = 0, wait_slot = 0, pending = 0;
+    __device__ __forceinline__ void init(uint64_t *bars, int lane) {
+        bar = bars;
+        if (lane == 0)
+            for (int k = 0; k < S; ++k) mbar_init(bar + k);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        __syncwarp();
     }
-    copy_row_edge(dst, c0, nchunks, lo, hi, lane);
-}
+    // after this lane staged its plane's row into slot issue_slot
+    __device__ __forceinline__ void commit(int lane) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar + issue_slot);
+        issue_slot = issue_slot + 1 == S ? 0 : issue_slot + 1;
+        ++pending;
+    }
+    __device__ __forceinline__ bool wait() {
+        const bool ok = mbar_wait_warp(bar + wait_slot, (phase >> wait_slot) & 1u);
+        if (ok) {
+            phase ^= 1u << wait_slot;
+            wait_slot = wait_slot + 1 == S ? 0 : wait_slot + 1;
+            --pending;
+        }
+        __syncwarp();
+        return ok;
+    }
+    // After a wait gave up: wait (again bounded) for the other rows in flight.
+    __device__ __forceinline__ void drain() {
+        while (pending > 0) {
+            mbar_wait_warp(bar + wait_slot, (phase >> wait_slot) & 1u);
+            phase ^= 1u << wait_slot;
+            wait_slot = wait_slot + 1 == S ? 0 : wait_slot + 1;
+            --pending;
+        }
+    }
+};
 
 // NW 32-bit words of a staged row starting at byte offset off (one offset per
 // image row, the same for every lane, so the branches are uniform).  Lanes
@@ -376,7 +451,7 @@ __device__ __forceinline__ void read_words(const unsigned char *base, int off, u
 #pragma unroll
         for (int k = 0; k <= NW; ++k) t[k] = (s & 8) ? t[k + 2] : t[k];
 #pragma unroll
-        for (int k = 0; k < NW; ++k) w[k] = sh ? __funnelshift_r(t[k], t[k + 1], sh) : t[k];
+        for (int k = 0; k < NW; ++k) w[k] = __funnelshift_r(t[k], t[k + 1], sh);  // sh = 0: t[k]
     } else {
         static_assert(NW == 2, "read_words: NW is 2 or a multiple of 4");
         const unsigned char *a = base + (off & ~7);
@@ -386,7 +461,7 @@ __device__ __forceinline__ void read_words(const unsigned char *base, int off, u
 #pragma unroll
         for (int k = 0; k < 3; ++k) t[k] = (off & 4) ? r[k + 1] : r[k];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) w[k] = sh ? __funnelshift_r(t[k], t[k + 1], sh) : t[k];
+        for (int k = 0; k < 2; ++k) w[k] = __funnelshift_r(t[k], t[k + 1], sh);
     }
 }
 
@@ -408,29 +483,36 @@ constexpr int kStrip = 32 * kLanePx;
 constexpr int kWinPerStrip = kStrip / kWin;
 constexpr int kImgRow = kStrip + 32;       // staged bytes per image row (alignment slack, 16-aligned)
 constexpr int kMsRow = kStrip / 2 + 32;    // staged bytes per MS row in the PAN pass
+constexpr int kGenWarps = 12;              // warps per CTA, unaligned path, 7-8 bands
 
 // Warps per CTA and ring depth: up to 6 bands, 16 warps with a 2-row ring
 // (more warps hide the row-shifting work of unaligned widths and the state
-// fits 128 registers); 7-8 bands, 8 warps with a 3-row ring.
-template <int NB>
+// fits 128 registers); 7-8 bands, 8 warps with a 3-row ring, or on the
+// unaligned path (kGenWarps) more warps with a 2-row ring.
+template <int NB, bool GEN>
 struct FastPan {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
-    static constexpr int kWarps = NB <= 6 ? 16 : 8;
+    static constexpr int kWarps = NB <= 6 ? 16 : (GEN ? kGenWarps : 8);
     static constexpr int kFastWarps = kWarps;
-    static constexpr int kStages = NB <= 6 ? 2 : 3;
+    static constexpr int kStages = NB <= 6 || GEN ? 2 : 3;
     static constexpr int kRowBytes = K * kImgRow + NB * kMsRow;
-    static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
-                                 kFastWarps * NB * 8;
+    static constexpr int kBarOffset = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
+                                      kFastWarps * NB * 8;
+    static constexpr int kSmem = kBarOffset + kFastWarps * kStages * 8;  // with the mbarriers (GEN)
 };
 
 // GEN = false: rows of every plane start on 16-byte boundaries (W % 16 == 0,
-// aligned planes): one chunk per lane and image, read back by the same lane.
-// GEN = true: any width and alignment, rows shifted into place.
+// aligned planes): one cp.async chunk per lane and image, read back by the
+// same lane.  GEN = true: any width and alignment; lane p stages plane p's row
+// (fused bands, PAN, then the MS bands) with one bulk copy, and every lane
+// shifts its words into place when it reads them.  A bulk-copy wait that gives
+// up (about a second) stops the warp and is reported in the CTA's partial row
+// (entry P + NB), which turns the figures into NaN.
 template <int NB, bool GEN>
-__global__ void __launch_bounds__(FastPan<NB>::kWarps * 32, 1)
+__global__ void __launch_bounds__(FastPan<NB, GEN>::kWarps * 32, 1)
 metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     allow_dependents();
-    using C = FastPan<NB>;
+    using C = FastPan<NB, GEN>;
     constexpr int kFastWarps = C::kWarps;
     constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -448,6 +530,24 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     const int64_t sx_n = (W + kStrip - 1) / kStrip, sy_n = (H + kWin - 1) / kWin;
     const int64_t items = sx_n * sy_n;
     const int64_t nw = (int64_t)gridDim.x * kFastWarps;
+    // GEN: this lane's plane -- fused band `lane`, PAN (lane NB, when Q is
+    // wanted), MS band lane - NB - 1 -- and where its rows go in a slot.
+    BulkRing<S> br;
+    const uint8_t *pl = nullptr;
+    int64_t pl_n = 0;
+    int kind = 0, dst_off = 0;  // kind 1: PAN-resolution row, 2: MS row
+    bool err = false;
+    if (GEN) {
+        br.init(reinterpret_cast<uint64_t *>(smem + C::kBarOffset) + warp * S, lane);
+        if (lane < NB) {
+            pl = F + (int64_t)lane * HW; pl_n = HW; kind = 1; dst_off = lane * kImgRow;
+        } else if (lane == NB) {
+            if (a.want_q) { pl = pan; pl_n = HW; kind = 1; dst_off = NB * kImgRow; }
+        } else if (lane <= 2 * NB) {
+            const int b = lane - NB - 1;
+            pl = static_cast<const uint8_t *>(a.ms[b]); pl_n = H2 * W2; kind = 2; dst_off = K * kImgRow + b * kMsRow;
+        }
+    }
     for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
         const int64_t x0 = (it % sx_n) * kStrip;
         const int64_t x = x0 + kLanePx * lane;
@@ -458,26 +558,25 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
         const bool full = a.want_q && (y0 + kWin <= H) && (xwin + kWin <= W);
         const int nrows = (int)min((int64_t)kWin, H - y0);
         const int span = (int)min((int64_t)kStrip, W - x0);
-        // Row r of this strip into ring slot r % S.
+        // Row r of this strip into the next ring slot (r % S on the aligned path).
         auto issue = [&](int r) {
+            if (GEN) {
+                if (r < nrows) {
+                    unsigned char *slot = ring + br.issue_slot * RB;
+                    const int64_t y = y0 + r;
+                    if (kind == 1)
+                        stage_row(slot + dst_off, pl + y * W + x0, span, pl, pl + pl_n, br.bar + br.issue_slot);
+                    else if (kind == 2)
+                        stage_row(slot + dst_off, pl + (y >> 1) * W2 + (x0 >> 1), span / 2, pl, pl + pl_n,
+                                  br.bar + br.issue_slot);
+                    br.commit(lane);
+                }
+                return;
+            }
             if (r < nrows) {
                 unsigned char *slot = ring + (r % S) * RB;
                 const int64_t y = y0 + r;
-                if (GEN) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const uint8_t *plane = F + (int64_t)b * HW;
-                        copy_row<kStrip / 16 + 1>(slot + b * kImgRow, plane + y * W + x0, span, plane, plane + HW, lane);
-                    }
-                    if (a.want_q)
-                        copy_row<kStrip / 16 + 1>(slot + NB * kImgRow, pan + y * W + x0, span, pan, pan + HW, lane);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
-                        copy_row<kStrip / 32 + 1>(slot + K * kImgRow + b * kMsRow, m + (y >> 1) * W2 + (x0 >> 1),
-                                                  span / 2, m, m + H2 * W2, lane);
-                    }
-                } else if (act) {
+                if (act) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
                         cp_async16(slot + b * kImgRow + lane * 16, F + (int64_t)b * HW + y * W + x, 16u);
@@ -500,22 +599,42 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) se[b] = 0;
         for (int r = 0; r < nrows; ++r) {
-            if (GEN) __syncwarp();  // every lane is done with the slot refilled next
-            issue(r + S - 1);
-            cp_async_wait<S - 1>();
-            if (GEN) __syncwarp();  // every lane's copies of row r are in place
-            if (!act) continue;
-            const unsigned char *slot = ring + (r % S) * RB;
+            const unsigned char *slot;
             const int64_t y = y0 + r;
+            int my_o = 0;  // GEN: offset of this lane's plane row in its staged slot
+            if (GEN) {
+                __syncwarp();  // every lane is done with the slot refilled next
+                issue(r + S - 1);
+                const int rs = br.wait_slot;
+                if (!br.wait()) {
+                    err = true;
+                    break;
+                }
+                slot = ring + rs * RB;
+                const unsigned rowbase = kind == 2 ? (unsigned)(y >> 1) * (unsigned)W2 + (unsigned)(x0 >> 1)
+                                                   : (unsigned)y * (unsigned)W + (unsigned)x0;
+                my_o = (int)(((unsigned)reinterpret_cast<uintptr_t>(pl) + rowbase) & 15u);
+            } else {
+                issue(r + S - 1);
+                cp_async_wait<S - 1>();
+                slot = ring + (r % S) * RB;
+            }
+            int o_f[NB], o_m[NB], o_p = 0;
+            if (GEN) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    o_f[b] = __shfl_sync(0xffffffffu, my_o, b);
+                    o_m[b] = __shfl_sync(0xffffffffu, my_o, NB + 1 + b);
+                }
+                o_p = __shfl_sync(0xffffffffu, my_o, NB);
+            }
+            if (!act) continue;
             uint32_t f[NB][4], m[NB][2];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 if (GEN) {
-                    const int offf = (int)(reinterpret_cast<uintptr_t>(F + (int64_t)b * HW + y * W + x0) & 15) + kLanePx * lane;
-                    read_words<4>(slot + b * kImgRow, offf, f[b]);
-                    const uint8_t *mrow = static_cast<const uint8_t *>(a.ms[b]) + (y >> 1) * W2 + (x0 >> 1);
-                    const int offm = (int)(reinterpret_cast<uintptr_t>(mrow) & 15) + (kLanePx / 2) * lane;
-                    read_words<2>(slot + K * kImgRow + b * kMsRow, offm, m[b]);
+                    read_words<4>(slot + b * kImgRow, o_f[b] + kLanePx * lane, f[b]);
+                    read_words<2>(slot + K * kImgRow + b * kMsRow, o_m[b] + (kLanePx / 2) * lane, m[b]);
                 } else {
                     const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + b * kImgRow + lane * 16);
                     f[b][0] = q4.x; f[b][1] = q4.y; f[b][2] = q4.z; f[b][3] = q4.w;
@@ -537,8 +656,7 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
             if (full) {
                 uint32_t pw[4];
                 if (GEN) {
-                    const int offp = (int)(reinterpret_cast<uintptr_t>(pan + y * W + x0) & 15) + kLanePx * lane;
-                    read_words<4>(slot + NB * kImgRow, offp, pw);
+                    read_words<4>(slot + NB * kImgRow, o_p + kLanePx * lane, pw);
                 } else {
                     const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + NB * kImgRow + lane * 16);
                     pw[0] = q4.x; pw[1] = q4.y; pw[2] = q4.z; pw[3] = q4.w;
@@ -570,7 +688,11 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
                 }
             }
         }
-        cp_async_wait<0>();
+        if (GEN && err) {
+            br.drain();
+            break;
+        }
+        if (!GEN) cp_async_wait<0>();
 #pragma unroll
         for (int b = 0; b < NB; ++b) se_tot[b] += (double)(unsigned)se[b];
         if (!__any_sync(0xffffffffu, full)) continue;
@@ -608,9 +730,10 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) sse[warp * NB + b] = v;
     }
-    __syncthreads();
+    const int any_err = __syncthreads_or(err);
     const float *sq0 = reinterpret_cast<const float *>(smem + kFastWarps * S * RB);
     double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    if (GEN && threadIdx.x == 0) out[P + NB] = any_err ? 1.0 : 0.0;
     for (int k = threadIdx.x; k < P + NB; k += kFastWarps * 32) {
         double acc = 0.0;
         for (int w = 0; w < kFastWarps; ++w) {
@@ -624,27 +747,30 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     }
 }
 
-template <int NB>
+template <int NB, bool GEN>
 struct FastMs {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
-    static constexpr int kWarps = NB <= 6 ? 16 : 8;
+    static constexpr int kWarps = NB <= 6 ? 16 : (GEN ? kGenWarps : 8);
     static constexpr int kFastWarps = kWarps;
-    static constexpr int kStages = NB <= 6 ? 2 : 3;
+    static constexpr int kStages = NB <= 6 || GEN ? 2 : 3;
     static constexpr int kPanRow = 2 * kStrip + 32;  // 32 PAN pixels per lane
     static constexpr int kRowBytes = NB * kImgRow + 2 * kPanRow;
-    static constexpr int kSmem = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
-                                 kFastWarps * NB * 8;
+    static constexpr int kBarOffset = kFastWarps * kStages * kRowBytes + kFastWarps * kWinPerStrip * P * 4 +
+                                      kFastWarps * NB * 8;
+    static constexpr int kSmem = kBarOffset + kFastWarps * kStages * 8;  // with the mbarriers (GEN)
 };
 
 // MS-resolution pass, 8-bit: a lane owns 16 MS pixels of an MS row (and the
 // 2 x 32 PAN pixels above them).  MS values are signed bytes (dp4a); PAN~ is
 // carried as Z = 4 PAN~ - 512 (the 2x2 sum, exact) and its products use
 // integer multiply-adds.
-// GEN as for the PAN pass (aligned: W % 32 == 0, 16-byte aligned MS and PAN).
+// GEN as for the PAN pass (aligned: W % 32 == 0, 16-byte aligned MS and PAN);
+// on the GEN path lane b stages MS band b's row and lanes NB, NB + 1 the two
+// PAN rows above it.
 template <int NB, bool GEN>
-__global__ void __launch_bounds__(FastMs<NB>::kWarps * 32, 1)
+__global__ void __launch_bounds__(FastMs<NB, GEN>::kWarps * 32, 1)
 metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
-    using C = FastMs<NB>;
+    using C = FastMs<NB, GEN>;
     constexpr int kFastWarps = C::kWarps;
     constexpr int K = C::K, P = C::P, S = C::kStages, RB = C::kRowBytes, PR = C::kPanRow;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -661,6 +787,19 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
     const int64_t sx_n = (W2 + kStrip - 1) / kStrip, sy_n = (H2 + kWin - 1) / kWin;
     const int64_t items = sx_n * sy_n;
     const int64_t nw = (int64_t)gridDim.x * kFastWarps;
+    BulkRing<S> br;
+    const uint8_t *pl = nullptr;
+    int64_t pl_n = 0;
+    int kind = 0, dst_off = 0;  // kind 1: MS row, 2: PAN row 2i + (lane - NB)
+    bool err = false;
+    if (GEN) {
+        br.init(reinterpret_cast<uint64_t *>(smem + C::kBarOffset) + warp * S, lane);
+        if (lane < NB) {
+            pl = static_cast<const uint8_t *>(a.ms[lane]); pl_n = H2 * W2; kind = 1; dst_off = lane * kImgRow;
+        } else if (lane < NB + 2) {
+            pl = pan; pl_n = HW; kind = 2; dst_off = NB * kImgRow + (lane - NB) * PR;
+        }
+    }
     for (int64_t it = (int64_t)blockIdx.x * kFastWarps + warp; it < items; it += nw) {
         const int64_t j0 = (it % sx_n) * kStrip;
         const int64_t j = j0 + kLanePx * lane;  // MS column
@@ -673,22 +812,23 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
         const int nrows = (int)min((int64_t)kWin, H2 - i0);
         const int span = (int)min((int64_t)kStrip, W2 - j0);
         auto issue = [&](int r) {
+            if (GEN) {
+                if (r < nrows) {
+                    unsigned char *slot = ring + br.issue_slot * RB;
+                    const int64_t i = i0 + r;
+                    if (kind == 1)
+                        stage_row(slot + dst_off, pl + i * W2 + j0, span, pl, pl + pl_n, br.bar + br.issue_slot);
+                    else if (kind == 2 && any_full)
+                        stage_row(slot + dst_off, pl + (2 * i + (lane - NB)) * W + 2 * j0, 2 * span, pl, pl + pl_n,
+                                  br.bar + br.issue_slot);
+                    br.commit(lane);
+                }
+                return;
+            }
             if (r < nrows) {
                 unsigned char *slot = ring + (r % S) * RB;
                 const int64_t i = i0 + r;
-                if (GEN) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        const uint8_t *m = static_cast<const uint8_t *>(a.ms[b]);
-                        copy_row<kStrip / 16 + 1>(slot + b * kImgRow, m + i * W2 + j0, span, m, m + H2 * W2, lane);
-                    }
-                    if (any_full) {
-                        copy_row<kStrip / 8 + 1>(slot + NB * kImgRow, pan + (2 * i) * W + 2 * j0, 2 * span, pan,
-                                                 pan + HW, lane);
-                        copy_row<kStrip / 8 + 1>(slot + NB * kImgRow + PR, pan + (2 * i + 1) * W + 2 * j0, 2 * span,
-                                                 pan, pan + HW, lane);
-                    }
-                } else if (act) {
+                if (act) {
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
                         cp_async16(slot + b * kImgRow + lane * 16, static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j, 16u);
@@ -713,19 +853,39 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) sm[b] = 0;
         for (int r = 0; r < nrows; ++r) {
-            if (GEN) __syncwarp();
-            issue(r + S - 1);
-            cp_async_wait<S - 1>();
-            if (GEN) __syncwarp();
-            if (!act) continue;
-            const unsigned char *slot = ring + (r % S) * RB;
+            const unsigned char *slot;
             const int64_t i = i0 + r;
+            int my_o = 0;  // GEN: offset of this lane's plane row in its staged slot
+            if (GEN) {
+                __syncwarp();  // every lane is done with the slot refilled next
+                issue(r + S - 1);
+                const int rs = br.wait_slot;
+                if (!br.wait()) {
+                    err = true;
+                    break;
+                }
+                slot = ring + rs * RB;
+                const unsigned rowbase = kind == 2 ? (unsigned)(2 * i + (lane - NB)) * (unsigned)W + (unsigned)(2 * j0)
+                                                   : (unsigned)i * (unsigned)W2 + (unsigned)j0;
+                my_o = (int)(((unsigned)reinterpret_cast<uintptr_t>(pl) + rowbase) & 15u);
+            } else {
+                issue(r + S - 1);
+                cp_async_wait<S - 1>();
+                slot = ring + (r % S) * RB;
+            }
+            int o_m[NB], o_p0 = 0, o_p1 = 0;
+            if (GEN) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) o_m[b] = __shfl_sync(0xffffffffu, my_o, b);
+                o_p0 = __shfl_sync(0xffffffffu, my_o, NB);
+                o_p1 = __shfl_sync(0xffffffffu, my_o, NB + 1);
+            }
+            if (!act) continue;
             uint32_t mv[NB][4];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 if (GEN) {
-                    const uint8_t *mrow = static_cast<const uint8_t *>(a.ms[b]) + i * W2 + j0;
-                    read_words<4>(slot + b * kImgRow, (int)(reinterpret_cast<uintptr_t>(mrow) & 15) + kLanePx * lane, mv[b]);
+                    read_words<4>(slot + b * kImgRow, o_m[b] + kLanePx * lane, mv[b]);
                 } else {
                     const uint4 q4 = *reinterpret_cast<const uint4 *>(slot + b * kImgRow + lane * 16);
                     mv[b][0] = q4.x; mv[b][1] = q4.y; mv[b][2] = q4.z; mv[b][3] = q4.w;
@@ -737,10 +897,8 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
             if (!full) continue;
             uint32_t r0[8], r1[8];
             if (GEN) {
-                read_words<8>(slot + NB * kImgRow,
-                              (int)(reinterpret_cast<uintptr_t>(pan + (2 * i) * W + 2 * j0) & 15) + 2 * kLanePx * lane, r0);
-                read_words<8>(slot + NB * kImgRow + PR,
-                              (int)(reinterpret_cast<uintptr_t>(pan + (2 * i + 1) * W + 2 * j0) & 15) + 2 * kLanePx * lane, r1);
+                read_words<8>(slot + NB * kImgRow, o_p0 + 2 * kLanePx * lane, r0);
+                read_words<8>(slot + NB * kImgRow + PR, o_p1 + 2 * kLanePx * lane, r1);
             } else {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
@@ -790,7 +948,11 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
                 }
             }
         }
-        cp_async_wait<0>();
+        if (GEN && err) {
+            br.drain();
+            break;
+        }
+        if (!GEN) cp_async_wait<0>();
 #pragma unroll
         for (int b = 0; b < NB; ++b) sum_tot[b] += (double)(unsigned)sm[b];
         if (!any_full) continue;
@@ -826,9 +988,10 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) ssum[warp * NB + b] = v;
     }
-    __syncthreads();
+    const int any_err = __syncthreads_or(err);
     const float *sq0 = reinterpret_cast<const float *>(smem + kFastWarps * S * RB);
     double *out = a.partial + (int64_t)blockIdx.x * a.stride;
+    if (GEN && threadIdx.x == 0) out[P + NB] = any_err ? 1.0 : 0.0;
     for (int k = threadIdx.x; k < P + NB; k += kFastWarps * 32) {
         double acc = 0.0;
         for (int w = 0; w < kFastWarps; ++w) {
@@ -938,7 +1101,9 @@ metrics_ms_kernel(const __grid_constant__ MetricArgs a) {
 
 // One CTA: sums the per-CTA partial rows and writes out[0..3] = ERGAS, QNR,
 // D_lambda, D_s (QNR terms NaN when not requested or when no full window
-// exists at either resolution).  Each warp reduces one column of partials:
+// exists at either resolution; all four NaN when a pass flagged in
+// `status_mask` (bit 0 PAN-resolution, bit 1 MS) reported a wait that gave up
+// in entry P + nb of a partial row).  Each warp reduces one column of partials:
 // lanes stride over the CTAs, then a xor butterfly (a fixed order, so the
 // result is the same on every run).  The lane loop is unrolled so that its
 // loads are in flight together: the partials sit in L2 and each round trip
@@ -947,17 +1112,17 @@ constexpr int kFinalizeThreads = 1024;
 __global__ void __launch_bounds__(kFinalizeThreads)
 metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_pan, const int *ctas_pan_dev,
                         int ctas_ms, int stride, int nb, int want_q, int64_t H, int64_t W, int64_t nwin_pan,
-                        int64_t nwin_ms, double *out) {
+                        int64_t nwin_ms, int status_mask, double *out) {
     if (ctas_pan_dev) ctas_pan = *ctas_pan_dev;
     __shared__ double tot_pan[64 + kMaxBands];
     __shared__ double tot_ms[64 + kMaxBands];
     const int P = nb * (nb - 1) / 2 + nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int k = warp; k < 2 * (P + nb); k += nwarps) {
-        const bool ms = k >= P + nb;
-        const int kk = ms ? k - (P + nb) : k;
+    for (int k = warp; k < 2 * (P + nb + 1); k += nwarps) {
+        const bool ms = k >= P + nb + 1;
+        const int kk = ms ? k - (P + nb + 1) : k;
         const double *part = ms ? ms_part : pan_part;
-        const int ctas = ms ? ctas_ms : ctas_pan;
+        const int ctas = (kk < P + nb || ((status_mask >> (ms ? 1 : 0)) & 1)) ? (ms ? ctas_ms : ctas_pan) : 0;
         double a = 0.0;
 #pragma unroll 8
         for (int c = lane; c < ctas; c += 32) a += part[(int64_t)c * stride + kk];
@@ -989,6 +1154,10 @@ metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_
         ds += __shfl_xor_sync(0xffffffffu, ds, o);
     }
     if (lane != 0) return;
+    if (tot_pan[P + nb] + tot_ms[P + nb] > 0.0) {
+        out[0] = out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     out[0] = 100.0 * 0.5 * sqrt(e / nb);
     if (!q_ok) {
         out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
@@ -1026,11 +1195,13 @@ struct FastFn {
 };
 template <int NB, bool GEN>
 FastFn pan_u8_fn() {
-    return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB, GEN>), FastPan<NB>::kSmem, FastPan<NB>::kWarps};
+    return {reinterpret_cast<const void *>(&metrics_pan_u8_kernel<NB, GEN>),
+            GEN ? FastPan<NB, GEN>::kSmem : FastPan<NB, GEN>::kBarOffset, FastPan<NB, GEN>::kWarps};
 }
 template <int NB, bool GEN>
 FastFn ms_u8_fn() {
-    return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB, GEN>), FastMs<NB>::kSmem, FastMs<NB>::kWarps};
+    return {reinterpret_cast<const void *>(&metrics_ms_u8_kernel<NB, GEN>),
+            GEN ? FastMs<NB, GEN>::kSmem : FastMs<NB, GEN>::kBarOffset, FastMs<NB, GEN>::kWarps};
 }
 template <bool GEN>
 FastFn fast_fn_g(bool ms_pass, int nb) {
@@ -1114,13 +1285,14 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     double *out = m.workspace;
     double *pan_part = m.workspace + kMetricPanPartialOffset;
     double *ms_part = pan_part + (int64_t)kMetricMaxCtas * kMetricStride;
-    int gp = 0, gm = 0;
+    int gp = 0, gm = 0, status_mask = 0;
     cudaError_t e;
     // PAN-resolution pass (unless the fused forward + metrics kernel wrote it)
     if (m.pan_done) {
         e = cudaSuccess;
     } else if (fast) {
         const FastFn fp = fast_fn(false, m.bands, m.a16 != 0);
+        if (!m.a16) status_mask |= 1;
         const int64_t items = ((m.W + kStrip - 1) / kStrip) * ((m.H + kWin - 1) / kWin);
         e = fast_grid(fp, items, &gp);
         if (e != cudaSuccess) return e;
@@ -1146,6 +1318,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     void *args2[] = {&b};
     if (!m.in_f32) {
         const FastFn fm = fast_fn(true, m.bands, m.a32_ms != 0);
+        if (!m.a32_ms) status_mask |= 2;
         const int64_t items = ((m.W / 2 + kStrip - 1) / kStrip) * ((m.H / 2 + kWin - 1) / kWin);
         e = fast_grid(fm, items, &gm);
         if (e != cudaSuccess) return e;
@@ -1177,7 +1350,8 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     const int64_t nwp = (m.H / kWin) * (m.W / kWin), nwm = (m.H / 2 / kWin) * (m.W / 2 / kWin);
     const int *gp_dev = m.pan_done ? reinterpret_cast<const int *>(m.workspace + kMetricPanCtasSlot) : nullptr;
     metrics_finalize_kernel<<<1, kFinalizeThreads, 0, stream>>>(pan_part, ms_part, gp, gp_dev, gm, kMetricStride,
-                                                                m.bands, m.want_q, m.H, m.W, nwp, nwm, out);
+                                                                m.bands, m.want_q, m.H, m.W, nwp, nwm, status_mask,
+                                                                out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (m.result && m.result != out)

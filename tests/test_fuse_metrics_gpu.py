@@ -172,3 +172,31 @@ def test_two_call_form_rejects_unsupported(ws):
     ou = torch.empty((7, 64, 96), dtype=torch.uint8, device=DEV)
     with pytest.raises(_C.DwtfuseError):
         _C.dwtfuse_fuse_and_score(pan, ms, O.D4, None, ou, ws)
+
+
+def test_benchmark_step_full_size(ws):
+    """The benchmark step as timed (D4, PAN 16384^2 uint8, 6 MS bands 8192^2,
+    float32 + uint8 outputs, one dwtfuse_fuse_metrics call): outputs equal the
+    plain forward's bits, the metrics equal the oracle's on the whole images,
+    and sampled float32 pixels equal the oracle's point-wise closed form."""
+    H = W = 16384
+    pan, ms = scenegen.make_scene(H, W, 6, seed=0, blob_scale=16.0, device=DEV)
+    of, ou, r = fused_path(pan, ms, O.D4, ws)
+    f2 = torch.empty_like(of)
+    u2 = torch.empty_like(ou)
+    _C.dwtfuse_fuse(pan, ms, O.D4, f2, u2)
+    torch.cuda.synchronize()
+    assert torch.equal(of, f2) and torch.equal(ou, u2)
+    del f2, u2
+    rng = np.random.default_rng(5)
+    p, m = pan.cpu().numpy(), ms.cpu().numpy()
+    ii, jj = rng.integers(0, H, 64), rng.integers(0, W, 64)
+    for b in range(6):
+        ref = O.fuse_points(p, m[b], O.D4, ii, jj)
+        got = of[b].cpu().numpy()[ii, jj]
+        assert np.abs(got - ref).max() <= 5e-4
+    f = ou.cpu().numpy()
+    q, dl, ds = O.qnr(f, list(m), p)
+    ref = np.array([O.ergas(f, list(m)), q, dl, ds])
+    assert abs(r[0] - ref[0]) <= 1e-12 * ref[0], (r, ref)
+    assert np.abs(r[1:] - ref[1:]).max() <= 2e-6, (r, ref)
