@@ -760,10 +760,19 @@ struct FastMs {
     static constexpr int kSmem = kBarOffset + kFastWarps * kStages * 8;  // with the mbarriers (GEN)
 };
 
+// Signed bytes of a times unsigned bytes of b, summed into c.
+__device__ __forceinline__ int dp4a_su(int a, uint32_t b, int c) {
+    int d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
 // MS-resolution pass, 8-bit: a lane owns 16 MS pixels of an MS row (and the
 // 2 x 32 PAN pixels above them).  MS values are signed bytes (dp4a); PAN~ is
-// carried as Z = 4 PAN~ - 512 (the 2x2 sum, exact) and its products use
-// integer multiply-adds.
+// carried as Z = 4 PAN~ - 512 (the 2x2 sum, exact).  The MS x PAN~ sums are
+// taken as sum v (P_tl + P_tr + P_bl + P_br) by four mixed-sign dp4a over the
+// words of the blocks' four corner pixels, and the -512 sum v term is
+// subtracted from the window totals (sum v is the band's s1).
 // GEN as for the PAN pass (aligned: W % 32 == 0, 16-byte aligned MS and PAN);
 // on the GEN path lane b stages MS band b's row and lanes NB, NB + 1 the two
 // PAN rows above it.
@@ -912,6 +921,9 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
             for (int q = 0; q < 4; ++q) {
                 // PAN words of rows 2i, 2i+1 covering MS pixels 4q .. 4q+3
                 const uint32_t ua = r0[2 * q], ub = r0[2 * q + 1], la = r1[2 * q], lb = r1[2 * q + 1];
+                // the four corner pixels of MS pixels 4q .. 4q+3's PAN blocks
+                const uint32_t ptl = __byte_perm(ua, ub, 0x6420u), ptr = __byte_perm(ua, ub, 0x7531u);
+                const uint32_t pbl = __byte_perm(la, lb, 0x6420u), pbr = __byte_perm(la, lb, 0x7531u);
                 int z[4];
                 z[0] = (int)__dp4a(__byte_perm(ua, la, 0x5410u), 0x01010101u, 0u) - 512;
                 z[1] = (int)__dp4a(__byte_perm(ua, la, 0x7632u), 0x01010101u, 0u) - 512;
@@ -941,10 +953,8 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
                 for (int b = 0; b < NB; ++b) {
                     const int idx = NB * (NB - 1) / 2 + b;
-                    // signed bytes of v[b] times Z
-                    const int w = v[b];
-                    sxy[idx] += ((w << 24) >> 24) * z[0] + ((w << 16) >> 24) * z[1] +
-                                ((w << 8) >> 24) * z[2] + (w >> 24) * z[3];
+                    // signed bytes of v[b] times the 2x2 PAN sums (the -512 part at the window total)
+                    sxy[idx] = dp4a_su(v[b], pbr, dp4a_su(v[b], pbl, dp4a_su(v[b], ptr, dp4a_su(v[b], ptl, sxy[idx]))));
                 }
             }
         }
@@ -977,7 +987,7 @@ metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int idx = NB * (NB - 1) / 2 + b;
-            const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1);
+            const int Sxy = sxy[idx] + __shfl_xor_sync(0xffffffffu, sxy[idx], 1) - 512 * S1[b];
             const float qv = q_exact(S1[b], S2[b], S1[NB], S2[NB], Sxy, 4);
             if (leader) slotq[idx] += qv;
         }
