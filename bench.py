@@ -709,6 +709,51 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_case(args) -> None:
+    """One library call on a seeded synthetic scene, timed alone (for profiling
+    a single kernel family at a chosen size; not the benchmark line).  Prints
+    one JSON line: mean milliseconds per call and its algorithmic bytes / s."""
+    import torch
+
+    import scenegen
+    from paper_1803_00737_gb300 import _C, build as bld
+
+    bld.build()
+    dev = "cuda"
+    H, W, B = args.side, args.width or args.side, args.bands
+    pan, ms = scenegen.make_scene(H, W, B, seed=0, blob_scale=BLOB_SCALE, device=dev)
+    if args.case == "metrics":
+        fused = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+        _C.dwtfuse_fuse(pan, ms, WAVELET, None, fused)
+        ws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
+        res = torch.zeros(4, dtype=torch.float64, device=dev)
+        call = lambda: _C.dwtfuse_metrics(fused, ms, pan, ws, res)  # noqa: E731
+        nbytes = H * W * (B + 1 + B * 0.25) + H * W * (B * 0.25 + 1)
+    elif args.case == "fuse":
+        of = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+        ou = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+        call = lambda: _C.dwtfuse_fuse(pan, ms, WAVELET, of, ou)  # noqa: E731
+        nbytes = H * W * (1.0 + B * (0.25 + 4.0 + 1.0))
+    else:  # backward
+        g = scenegen.target_like((B, H, W), seed=1000, device=dev)
+        gp = torch.empty((H, W), dtype=torch.float32, device=dev)
+        gm = torch.empty((B, H // 2, W // 2), dtype=torch.float32, device=dev)
+        call = lambda: _C.dwtfuse_fuse_backward(g, WAVELET, gp, gm)  # noqa: E731
+        nbytes = H * W * (4.0 * B + 4.0 + B)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_call = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"case": args.case, "H": H, "W": W, "bands": B, "calls": args.steps, "ms": ms_call,
+                      "algorithmic_GBps": nbytes / (ms_call / 1e3) / 1e9}))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -727,8 +772,14 @@ def main() -> None:
                     help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
+    ap.add_argument("--case", choices=["metrics", "fuse", "backward"],
+                    help="time one library call alone at --side x --width with --bands (profiling aid)")
+    ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
+    ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

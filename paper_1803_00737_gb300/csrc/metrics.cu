@@ -415,10 +415,10 @@ struct BulkRing {
 
 // NW 32-bit words of a staged row starting at byte offset off (one offset per
 // image row, the same for every lane, so the branches are uniform).  Lanes
-// sit 4 NW bytes apart; an unaligned row is read as the aligned 16-byte (NW a
-// multiple of 4) or 8-byte (NW = 2) pieces that cover it, which keeps
-// consecutive lanes on consecutive banks, and the words are shifted into place
-// with uniform selects and funnel shifts.
+// sit 4 NW bytes apart.  An unaligned row is read as the NW + 1 words that
+// cover it (NW <= 4), or as the aligned 16-byte pieces that cover it (NW = 8,
+// where word loads would conflict 8 ways), and the words are shifted into
+// place with funnel shifts.
 template <int NW>
 __device__ __forceinline__ void read_words(const unsigned char *base, int off, uint32_t *w) {
     if (NW % 4 == 0 && (off & 15) == 0) {
@@ -436,7 +436,18 @@ __device__ __forceinline__ void read_words(const unsigned char *base, int off, u
         return;
     }
     const int sh = (off & 3) * 8;
-    if constexpr (NW % 4 == 0) {
+    if constexpr (NW <= 4) {
+        // lanes 4 NW bytes apart: word loads (2-way or 4-way bank conflicts)
+        // and funnel shifts cost fewer instructions than selecting words out of
+        // aligned vector loads
+        const uint32_t *a = reinterpret_cast<const uint32_t *>(base + (off & ~3));
+        uint32_t r[NW + 1];
+#pragma unroll
+        for (int k = 0; k <= NW; ++k) r[k] = a[k];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) w[k] = __funnelshift_r(r[k], r[k + 1], sh);  // sh = 0: r[k]
+    } else {
+        static_assert(NW % 4 == 0, "read_words: NW is 2, 4 or a multiple of 4");
         const unsigned char *a = base + (off & ~15);
         const int s = off & 15;
         uint32_t r[NW + 4];
@@ -452,16 +463,6 @@ __device__ __forceinline__ void read_words(const unsigned char *base, int off, u
         for (int k = 0; k <= NW; ++k) t[k] = (s & 8) ? t[k + 2] : t[k];
 #pragma unroll
         for (int k = 0; k < NW; ++k) w[k] = __funnelshift_r(t[k], t[k + 1], sh);  // sh = 0: t[k]
-    } else {
-        static_assert(NW == 2, "read_words: NW is 2 or a multiple of 4");
-        const unsigned char *a = base + (off & ~7);
-        const uint2 q0 = *reinterpret_cast<const uint2 *>(a), q1 = *reinterpret_cast<const uint2 *>(a + 8);
-        const uint32_t r[4] = {q0.x, q0.y, q1.x, q1.y};
-        uint32_t t[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) t[k] = (off & 4) ? r[k + 1] : r[k];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) w[k] = __funnelshift_r(t[k], t[k + 1], sh);
     }
 }
 
