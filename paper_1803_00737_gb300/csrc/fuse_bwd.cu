@@ -12,10 +12,14 @@
 //
 // Same warp-strip decomposition as the forward: a lane owns PAN columns
 // x..x+3 and walks down R MS rows.  Every band's two new PAN rows are loaded
-// together (all loads of a step in flight at once), and D4 keeps, per band, the
-// row low-pass of the two previous rows (a sliding vertical window), plus the
-// same for G, in registers.  Up to 4 bands per launch; further launches over
-// the remaining bands add their G - U(LL(G)) into grad_P.
+// together (all loads of a step in flight at once; D4 with 5-8 bands in two
+// groups of up to 4), and D4 keeps, per band, the row low-pass of the two
+// previous rows (a sliding vertical window), plus the same for G, in
+// registers.  Up to 8 bands per launch (4 on the W % 4 == 2 path, where the
+// 5-8 band bodies spill): chunks of 1-4 bands run 256-thread CTAs (two per SM,
+// 128 registers), chunks of 5-8 bands 384-thread CTAs (one per SM, 168
+// registers); further launches over the remaining bands add their
+// G - U(LL(G)) into grad_P.
 #include <cstring>
 
 #include "fuse_tile.cuh"
@@ -23,9 +27,11 @@
 
 namespace dwtfuse {
 
-constexpr int kBwdThreads = 256;
-constexpr int kBwdWarps = kBwdThreads / 32;
-constexpr int kBwdChunk = 4;  // bands per launch: every band's rows of a step stay in registers
+constexpr int kBwdThreads = 256;      // chunks of 1-4 bands
+constexpr int kBwdWideThreads = 384;  // chunks of 5-8 bands
+constexpr int kBwdChunk = 8;          // bands per launch
+constexpr int kBwdChunkAlt = 4;       // bands per launch, W % 4 == 2 with the shifted-row stores
+constexpr int kBwdGroup = 4;          // D4: bands whose rows of a step are loaded together
 
 struct BwdArgs {
     const float *g;               // [bands][H][W]
@@ -38,14 +44,14 @@ struct BwdArgs {
     int32_t ms2;                  // W/2 even and every gms 8-byte aligned: pair stores
     int32_t alt;                  // W % 4 == 2 with 16-byte aligned g / gpan: shifted odd rows
     int32_t wavelet;              // 0 Haar, 1 D4
+    int32_t chunk;                // bands per launch
+    int32_t b0;                   // first band of the chunk (batched tables)
 };
 
 // Scene table of one launch of the batched backward (band chunk b0 of n scenes).
 struct BwdBatchTable {
     int32_t n;
     int32_t R;
-    int32_t b0;
-    int32_t pad_;
     int64_t item_start[kMaxScenes + 1];
     int64_t strips_x[kMaxScenes];
     BwdArgs scenes[kMaxScenes];
@@ -147,26 +153,36 @@ __device__ __forceinline__ void haar_bwd_item(const BwdArgs &s, int64_t x0, int6
     const bool a4 = s.a4 != 0, pair = s.ms2 != 0;
     const bool lde = a4 || (ALT && s.alt != 0 && c.two);  // 4-pixel loads on even rows
     for (int64_t m = m_s; m < m_e; ++m) {
-        float p0[NB][4], p1[NB][4];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const float *gb = s.g + (int64_t)(b0 + b) * HW;
-            load_row4(gb + (2 * m) * W, c, lde, p0[b]);
-            load_row4(gb + (2 * m + 1) * W, c, a4, p1[b]);
-        }
-        if (!ALT && !c.active) continue;
         float g0[4] = {0.f, 0.f, 0.f, 0.f}, g1[4] = {0.f, 0.f, 0.f, 0.f};
+        // A group's two rows of every band in flight together.
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const float sA = (p0[b][0] + p0[b][1]) + (p1[b][0] + p1[b][1]);
-            const float sB = (p0[b][2] + p0[b][3]) + (p1[b][2] + p1[b][3]);
-            if (c.active) store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
+        for (int gs = 0; gs < NB; gs += kBwdGroup) {
+            constexpr int G = NB < kBwdGroup ? NB : kBwdGroup;
+            float p0[G][4], p1[G][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                g0[q] += p0[b][q];
-                g1[q] += p1[b][q];
+            for (int j = 0; j < G; ++j) {
+                if (gs + j < NB) {
+                    const float *gb = s.g + (int64_t)(b0 + gs + j) * HW;
+                    load_row4(gb + (2 * m) * W, c, lde, p0[j]);
+                    load_row4(gb + (2 * m + 1) * W, c, a4, p1[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int b = gs + j;
+                if (b >= NB) continue;
+                const float sA = (p0[j][0] + p0[j][1]) + (p1[j][0] + p1[j][1]);
+                const float sB = (p0[j][2] + p0[j][3]) + (p1[j][2] + p1[j][3]);
+                if (c.active)
+                    store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * 0.25f * sA, s.kappa * 0.25f * sB);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    g0[q] += p0[j][q];
+                    g1[q] += p1[j][q];
+                }
             }
         }
+        if (!ALT && !c.active) continue;
         const float mA = ((g0[0] + g0[1]) + (g1[0] + g1[1])) * 0.25f;
         const float mB = ((g0[2] + g0[3]) + (g1[2] + g1[3])) * 0.25f;
         const float v0[4] = {g0[0] - mA, g0[1] - mA, g0[2] - mB, g0[3] - mB};
@@ -252,34 +268,44 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
     }
 
     for (int64_t m = m_s; m < m_e; ++m) {
-        // Every band's PAN rows 2m+2 and 2m+3 in flight together.
-        float v[NB][2][8];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const float *gb = g + (int64_t)b * HW;
-            load_row8(gb + wrap(2 * m + 2, H) * W, c, lde, v[b][0]);
-            load_row8(gb + wrap(2 * m + 3, H) * W, c, a4, v[b][1]);
-        }
         float ga[2][8];
+        // A group's PAN rows 2m+2 and 2m+3 of every band in flight together.
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+        for (int g0 = 0; g0 < NB; g0 += kBwdGroup) {
+            constexpr int G = NB < kBwdGroup ? NB : kBwdGroup;
+            float v[G][2][8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) ga[r][k] = 0.f;
+            for (int j = 0; j < G; ++j) {
+                if (g0 + j < NB) {
+                    const float *gb = g + (int64_t)(g0 + j) * HW;
+                    load_row8(gb + wrap(2 * m + 2, H) * W, c, lde, v[j][0]);
+                    load_row8(gb + wrap(2 * m + 3, H) * W, c, a4, v[j][1]);
+                }
+            }
+            if (g0 == 0) {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            float n0[2], n1[2];
-            d4_rowpass2(v[b][0], n0);
-            d4_rowpass2(v[b][1], n1);
-            // LL(G_b)(m, n), (m, n+1): column low-pass over rows 2m .. 2m+3
-            const float llA = fmaf(kH3, n1[0], fmaf(kH2, n0[0], fmaf(kH1, rb[b][1][0], kH0 * rb[b][0][0])));
-            const float llB = fmaf(kH3, n1[1], fmaf(kH2, n0[1], fmaf(kH1, rb[b][1][1], kH0 * rb[b][0][1])));
-            if (c.active) store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * llA, s.kappa * llB);
-            rb[b][0][0] = n0[0]; rb[b][0][1] = n0[1];
-            rb[b][1][0] = n1[0]; rb[b][1][1] = n1[1];
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                ga[0][k] += v[b][0][k];
-                ga[1][k] += v[b][1][k];
+                    for (int k = 0; k < 8; ++k) ga[r][k] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                const int b = g0 + j;
+                if (b >= NB) continue;
+                float n0[2], n1[2];
+                d4_rowpass2(v[j][0], n0);
+                d4_rowpass2(v[j][1], n1);
+                // LL(G_b)(m, n), (m, n+1): column low-pass over rows 2m .. 2m+3
+                const float llA = fmaf(kH3, n1[0], fmaf(kH2, n0[0], fmaf(kH1, rb[b][1][0], kH0 * rb[b][0][0])));
+                const float llB = fmaf(kH3, n1[1], fmaf(kH2, n0[1], fmaf(kH1, rb[b][1][1], kH0 * rb[b][0][1])));
+                if (c.active) store_gms(s.gms[b0 + b] + m * W2, c, pair, s.kappa * llA, s.kappa * llB);
+                rb[b][0][0] = n0[0]; rb[b][0][1] = n0[1];
+                rb[b][1][0] = n1[0]; rb[b][1][1] = n1[1];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    ga[0][k] += v[j][0][k];
+                    ga[1][k] += v[j][1][k];
+                }
             }
         }
         float rn0[3], rn1[3], llg[3];
@@ -313,12 +339,21 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
     }
 }
 
+// Threads per CTA and CTAs per SM of a chunk's kernel (see above).
+template <int NB>
+struct BwdShape {
+    static constexpr int kThreads = NB <= 4 ? kBwdThreads : kBwdWideThreads;
+    static constexpr int kMinBlocks = NB <= 4 ? 2 : 1;
+    static constexpr int kWarps = kThreads / 32;
+};
+
 template <int WAV, int NB, bool ALT>
-__global__ void __launch_bounds__(kBwdThreads, 2)
+__global__ void __launch_bounds__(BwdShape<NB>::kThreads, BwdShape<NB>::kMinBlocks)
 fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t strips_x, int64_t items, int R) {
+    constexpr int kWarps = BwdShape<NB>::kWarps;
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * kBwdWarps;
-    for (int64_t it = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5); it < items; it += nwarps) {
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t it = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); it < items; it += nwarps) {
         const int64_t sx = it % strips_x, sy = it / strips_x;
         const int64_t m_s = sy * R;
         const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
@@ -329,11 +364,12 @@ fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t stri
     }
 }
 
-// Batched: launch `chunk` of a batched backward covers band chunk `chunk` of
-// every scene that has one (item ranges by prefix sums, an atomic queue as in
-// the batched forward); chunks after the first add into grad_P, so they run as
-// separate launches in order.
-__global__ void __launch_bounds__(kBwdThreads, 2)
+// Batched: a launch covers band chunk b0 of the scenes in its table whose
+// chunk has 1-4 bands (WIDE = false) or 5-8 bands (WIDE = true); item ranges by
+// prefix sums, an atomic queue as in the batched forward.  Chunks after the
+// first add into grad_P, so they run as later launches.
+template <bool WIDE>
+__global__ void __launch_bounds__(WIDE ? kBwdWideThreads : kBwdThreads, WIDE ? 1 : 2)
 fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long long *queue) {
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)t.item_start[t.n];
@@ -352,7 +388,8 @@ fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long l
         const int64_t sx = local % t.strips_x[lo], sy = local / t.strips_x[lo];
         const int64_t m_s = sy * t.R;
         const int64_t m_e = min(m_s + (int64_t)t.R, s.H >> 1);
-        const int b0 = t.b0, nb = min(s.bands - b0, kBwdChunk);
+        // the table holds a scene here only if its chunk has 1-4 (5-8 when WIDE) bands
+        const int b0 = s.b0, nb = min(s.bands - b0, WIDE ? kBwdChunk : kBwdGroup);
         const bool acc = b0 > 0, alt = s.alt != 0;
         const int64_t x0 = sx * kWarpCols;
 #define DWTFUSE_BWD_CASE(NBV)                                                                 \
@@ -365,11 +402,25 @@ fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long l
             else d4_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                      \
         }                                                                                     \
         break;
-        switch (nb) {
-            DWTFUSE_BWD_CASE(1) DWTFUSE_BWD_CASE(2) DWTFUSE_BWD_CASE(3) DWTFUSE_BWD_CASE(4)
-            default: break;
+#define DWTFUSE_BWD_WIDE_CASE(NBV)                                                            \
+    case NBV:                                                                                 \
+        if (s.wavelet == 0) haar_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);          \
+        else d4_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                           \
+        break;
+        if constexpr (WIDE) {  // never a shifted-row scene (those take chunks of 4)
+            switch (nb) {
+                DWTFUSE_BWD_WIDE_CASE(5) DWTFUSE_BWD_WIDE_CASE(6) DWTFUSE_BWD_WIDE_CASE(7)
+                DWTFUSE_BWD_WIDE_CASE(8)
+                default: break;
+            }
+        } else {
+            switch (nb) {
+                DWTFUSE_BWD_CASE(1) DWTFUSE_BWD_CASE(2) DWTFUSE_BWD_CASE(3) DWTFUSE_BWD_CASE(4)
+                default: break;
+            }
         }
 #undef DWTFUSE_BWD_CASE
+#undef DWTFUSE_BWD_WIDE_CASE
     }
 }
 
@@ -377,8 +428,12 @@ namespace {
 
 template <int WAV, int NB>
 const void *bwd_fn(bool alt) {
-    return alt ? reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, true>)
-               : reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
+    if constexpr (NB > kBwdChunkAlt) {  // shifted-row scenes take chunks of 4
+        return reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
+    } else {
+        return alt ? reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, true>)
+                   : reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
+    }
 }
 
 template <int WAV>
@@ -387,9 +442,16 @@ const void *bwd_fn_nb(int nb, bool alt) {
         case 1: return bwd_fn<WAV, 1>(alt);
         case 2: return bwd_fn<WAV, 2>(alt);
         case 3: return bwd_fn<WAV, 3>(alt);
-        default: return bwd_fn<WAV, 4>(alt);
+        case 4: return bwd_fn<WAV, 4>(alt);
+        case 5: return bwd_fn<WAV, 5>(alt);
+        case 6: return bwd_fn<WAV, 6>(alt);
+        case 7: return bwd_fn<WAV, 7>(alt);
+        default: return bwd_fn<WAV, 8>(alt);
     }
 }
+
+// Threads per CTA of a chunk of nb bands.
+int bwd_threads(int nb) { return nb <= 4 ? kBwdThreads : kBwdWideThreads; }
 
 }  // namespace
 
@@ -411,6 +473,7 @@ BwdArgs make_bwd_args(const float *g, int bands, int64_t H, int64_t W, int wavel
     const bool al16 = (reinterpret_cast<uintptr_t>(g) % 16 == 0) && (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.a4 = (W % 4 == 0) && al16;
     s.alt = (W % 4 == 2) && al16;
+    s.chunk = s.alt ? kBwdChunkAlt : kBwdChunk;
     s.ms2 = ms2;
     return s;
 }
@@ -419,44 +482,57 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
                                          cudaStream_t stream) {
     static thread_local BwdBatchTable t;  // ~28 KB: kept off the stack
     static thread_local BwdArgs scenes[kMaxScenes];
-    int max_bands = 0;
+    int max_chunks = 0;
     for (int i = 0; i < n; ++i) {
         scenes[i] = make_bwd_args(in[i].grad_out, in[i].bands, in[i].H, in[i].W, in[i].wavelet, in[i].grad_pan,
                                   in[i].grad_ms);
-        max_bands = in[i].bands > max_bands ? in[i].bands : max_bands;
+        const int nc = (scenes[i].bands + scenes[i].chunk - 1) / scenes[i].chunk;
+        max_chunks = nc > max_chunks ? nc : max_chunks;
     }
-    const void *fn = reinterpret_cast<const void *>(&fuse_bwd_batched_kernel);
-    int occ = 0, sms = 0;
-    cudaError_t e = resident_blocks(fn, kBwdThreads, &occ);
+    int sms = 0;
+    cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    e = sm_count(&sms);
-    if (e != cudaSuccess) return e;
-    const int64_t cap = (int64_t)sms * occ;
-    for (int b0 = 0; b0 < max_bands; b0 += kBwdChunk) {
-        std::memset(&t, 0, sizeof t);
-        t.R = kDefaultRows;
-        t.b0 = b0;
-        int64_t acc = 0;
-        int k = 0;
-        for (int i = 0; i < n; ++i) {
-            if (scenes[i].bands <= b0) continue;
-            const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
-            t.scenes[k] = scenes[i];
+    for (int chunk = 0; chunk < max_chunks; ++chunk) {
+        for (int wide = 0; wide < 2; ++wide) {  // scenes whose chunk has 1-4, then 5-8 bands
+            std::memset(&t, 0, sizeof t);
+            t.R = kDefaultRows;
+            int64_t acc = 0;
+            int k = 0;
+            for (int i = 0; i < n; ++i) {
+                const int b0 = chunk * scenes[i].chunk;
+                const int rest = scenes[i].bands - b0;
+                const int nb = rest < scenes[i].chunk ? rest : scenes[i].chunk;
+                if (nb <= 0 || (nb > 4) != (wide != 0)) continue;
+                const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
+                t.scenes[k] = scenes[i];
+                t.scenes[k].b0 = b0;
+                t.item_start[k] = acc;
+                t.strips_x[k] = g.strips_x;
+                acc += g.items;
+                ++k;
+            }
+            if (k == 0) continue;
+            t.n = k;
             t.item_start[k] = acc;
-            t.strips_x[k] = g.strips_x;
-            acc += g.items;
-            ++k;
+            const void *fn = wide ? reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<true>)
+                                  : reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<false>);
+            const int threads = wide ? kBwdWideThreads : kBwdThreads;
+            int occ = 0;
+            e = resident_blocks(fn, threads, &occ);
+            if (e != cudaSuccess) return e;
+            const int64_t cap = (int64_t)sms * occ;
+            const int64_t need = (acc + threads / 32 - 1) / (threads / 32);
+            const unsigned grid = (unsigned)(need < cap ? need : cap);
+            if (grid == 0) continue;
+            e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
+            if (e != cudaSuccess) return e;
+            if (wide)
+                fuse_bwd_batched_kernel<true><<<grid, kBwdWideThreads, 0, stream>>>(t, queue);
+            else
+                fuse_bwd_batched_kernel<false><<<grid, kBwdThreads, 0, stream>>>(t, queue);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
         }
-        t.n = k;
-        t.item_start[k] = acc;
-        const int64_t need = (acc + kBwdWarps - 1) / kBwdWarps;
-        const unsigned grid = (unsigned)(need < cap ? need : cap);
-        if (grid == 0) continue;
-        e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
-        if (e != cudaSuccess) return e;
-        fuse_bwd_batched_kernel<<<grid, kBwdThreads, 0, stream>>>(t, queue);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -467,22 +543,23 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    for (int b0 = 0; b0 < bands; b0 += kBwdChunk) {
-        const int nb = bands - b0 < kBwdChunk ? bands - b0 : kBwdChunk;
+    for (int b0 = 0; b0 < bands; b0 += s.chunk) {
+        const int nb = bands - b0 < s.chunk ? bands - b0 : s.chunk;
         const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb, s.alt != 0) : bwd_fn_nb<1>(nb, s.alt != 0);
+        const int threads = bwd_threads(nb), warps = threads / 32;
         int occ = 0;
-        e = resident_blocks(fn, kBwdThreads, &occ);
+        e = resident_blocks(fn, threads, &occ);
         if (e != cudaSuccess) return e;
         const int64_t cap = (int64_t)sms * occ;
-        int Rl = R > 0 ? R : balanced_rows(H, W, cap * kBwdWarps);
+        int Rl = R > 0 ? R : balanced_rows(H, W, cap * warps);
         const ItemGrid ig = item_grid(H, W, Rl);
-        const int64_t need = (ig.items + kBwdWarps - 1) / kBwdWarps;
+        const int64_t need = (ig.items + warps - 1) / warps;
         const unsigned grid = (unsigned)(need < cap ? need : cap);
         if (grid == 0) return cudaSuccess;
         int acc = b0 > 0;
         int64_t strips_x = ig.strips_x, items = ig.items;
         void *args[] = {&s, &b0, &acc, &strips_x, &items, &Rl};
-        e = cudaLaunchKernel(fn, dim3(grid), dim3(kBwdThreads), args, 0, stream);
+        e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

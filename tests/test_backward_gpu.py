@@ -37,7 +37,7 @@ def assert_close(got, ref):
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
 @pytest.mark.parametrize("shape", [(4, 4), (6, 18), (10, 6), (64, 64), (66, 258), (130, 250),
                                    (12, 814)])
-@pytest.mark.parametrize("B", [1, 4, 9])
+@pytest.mark.parametrize("B", [1, 4, 6, 9])
 def test_backward_matches_oracle_adjoint(wav, shape, B):
     rng = np.random.default_rng(abs(hash((wav, shape, B))) % 2**32)
     G = rng.standard_normal((B, *shape))
