@@ -12,14 +12,13 @@
 //
 // Same warp-strip decomposition as the forward: a lane owns PAN columns
 // x..x+3 and walks down R MS rows.  Every band's two new PAN rows are loaded
-// together (all loads of a step in flight at once; D4 with 5-8 bands in two
-// groups of up to 4), and D4 keeps, per band, the row low-pass of the two
-// previous rows (a sliding vertical window), plus the same for G, in
-// registers.  Up to 8 bands per launch (4 on the W % 4 == 2 path, where the
-// 5-8 band bodies spill): chunks of 1-4 bands run 256-thread CTAs (two per SM,
-// 128 registers), chunks of 5-8 bands 384-thread CTAs (one per SM, 168
-// registers); further launches over the remaining bands add their
-// G - U(LL(G)) into grad_P.
+// together in groups (D4: groups of 2 bands, or of 4 for 5-8 bands on
+// unshifted rows; measured fastest), and D4 keeps, per band, the row
+// low-pass of the two previous rows (a sliding vertical window), plus the
+// same for G, in registers.  Up to 8 bands per launch: chunks of 1-4 bands
+// run 256-thread CTAs (two per SM, 128 registers), chunks of 5-8 bands
+// 384-thread CTAs (one per SM, 168 registers); further launches over the
+// remaining bands add their G - U(LL(G)) into grad_P.
 #include <cstring>
 
 #include "fuse_tile.cuh"
@@ -30,8 +29,17 @@ namespace dwtfuse {
 constexpr int kBwdThreads = 256;      // chunks of 1-4 bands
 constexpr int kBwdWideThreads = 384;  // chunks of 5-8 bands
 constexpr int kBwdChunk = 8;          // bands per launch
-constexpr int kBwdChunkAlt = 4;       // bands per launch, W % 4 == 2 with the shifted-row stores
-constexpr int kBwdGroup = 4;          // D4: bands whose rows of a step are loaded together
+constexpr int kBwdGroup = 4;          // Haar: bands whose rows of a step are loaded together
+
+// D4: bands whose rows of a step are loaded together.  Fewer registers in
+// flight leave the compiler room to overlap the groups: groups of 2 beat all
+// bands at once for 3-4 bands (16384^2 x 4: 1.14 -> 1.00 ms) and for 5-8
+// bands on shifted rows (16384 x 16382 x 8: 2.81 -> 2.26 ms); 5-8 bands on
+// unshifted rows are fastest in groups of 4 (2.36 ms against 2.99).
+template <int NB, bool ALT>
+struct D4Group {
+    static constexpr int value = NB <= 2 ? NB : (NB <= 4 || ALT ? 2 : 4);
+};
 
 struct BwdArgs {
     const float *g;               // [bands][H][W]
@@ -197,7 +205,9 @@ __device__ __forceinline__ void d4_rowpass2(const float *v, float *r) {
     r[1] = fmaf(kH3, v[7], fmaf(kH2, v[6], fmaf(kH1, v[5], kH0 * v[4])));
 }
 
-template <int NB, bool ALT>
+// G: bands whose rows of a step are loaded together (the grouping changes
+// only the load schedule, not the arithmetic).
+template <int NB, bool ALT, int G = D4Group<NB, ALT>::value>
 __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_t m_s, int64_t m_e,
                                             int b0, bool acc, int lane) {
     const int64_t W = s.W, H = s.H, W2 = W >> 1, H2 = H >> 1, HW = H * W;
@@ -271,8 +281,7 @@ __device__ __forceinline__ void d4_bwd_item(const BwdArgs &s, int64_t x0, int64_
         float ga[2][8];
         // A group's PAN rows 2m+2 and 2m+3 of every band in flight together.
 #pragma unroll
-        for (int g0 = 0; g0 < NB; g0 += kBwdGroup) {
-            constexpr int G = NB < kBwdGroup ? NB : kBwdGroup;
+        for (int g0 = 0; g0 < NB; g0 += G) {
             float v[G][2][8];
 #pragma unroll
             for (int j = 0; j < G; ++j) {
@@ -364,11 +373,11 @@ fuse_bwd_kernel(const __grid_constant__ BwdArgs s, int b0, int acc, int64_t stri
     }
 }
 
-// Batched: a launch covers band chunk b0 of the scenes in its table whose
-// chunk has 1-4 bands (WIDE = false) or 5-8 bands (WIDE = true); item ranges by
-// prefix sums, an atomic queue as in the batched forward.  Chunks after the
-// first add into grad_P, so they run as later launches.
-template <bool WIDE>
+// Batched: a launch covers one band chunk of the scenes in its table of one
+// wavelet whose chunk has 1-4 bands (WIDE = false) or 5-8 bands (WIDE = true);
+// item ranges by prefix sums, an atomic queue as in the batched forward.
+// Chunks after the first add into grad_P, so they run as later launches.
+template <bool WIDE, int WAV>
 __global__ void __launch_bounds__(WIDE ? kBwdWideThreads : kBwdThreads, WIDE ? 1 : 2)
 fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long long *queue) {
     const int lane = threadIdx.x & 31;
@@ -394,23 +403,22 @@ fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long l
         const int64_t x0 = sx * kWarpCols;
 #define DWTFUSE_BWD_CASE(NBV)                                                                 \
     case NBV:                                                                                 \
-        if (s.wavelet == 0) {                                                                 \
+        if constexpr (WAV == 0) {                                                             \
             if (alt) haar_bwd_item<NBV, true>(s, x0, m_s, m_e, b0, acc, lane);                 \
             else haar_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                    \
         } else {                                                                              \
-            if (alt) d4_bwd_item<NBV, true>(s, x0, m_s, m_e, b0, acc, lane);                   \
-            else d4_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                      \
+            if (alt) d4_bwd_item<NBV, true, WIDE ? D4Group<NBV, true>::value : NBV>(           \
+                s, x0, m_s, m_e, b0, acc, lane);                                              \
+            else d4_bwd_item<NBV, false, WIDE ? D4Group<NBV, false>::value : NBV>(             \
+                s, x0, m_s, m_e, b0, acc, lane);                                              \
         }                                                                                     \
         break;
-#define DWTFUSE_BWD_WIDE_CASE(NBV)                                                            \
-    case NBV:                                                                                 \
-        if (s.wavelet == 0) haar_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);          \
-        else d4_bwd_item<NBV, false>(s, x0, m_s, m_e, b0, acc, lane);                           \
-        break;
-        if constexpr (WIDE) {  // never a shifted-row scene (those take chunks of 4)
+        // 1-4 bands: D4 loads every band's rows at once in this kernel (groups of
+        // 2, the per-scene kernel's choice, ran 13 % slower here: 0.625 against
+        // 0.551 ms for 8 x 4096^2 x 4).
+        if constexpr (WIDE) {
             switch (nb) {
-                DWTFUSE_BWD_WIDE_CASE(5) DWTFUSE_BWD_WIDE_CASE(6) DWTFUSE_BWD_WIDE_CASE(7)
-                DWTFUSE_BWD_WIDE_CASE(8)
+                DWTFUSE_BWD_CASE(5) DWTFUSE_BWD_CASE(6) DWTFUSE_BWD_CASE(7) DWTFUSE_BWD_CASE(8)
                 default: break;
             }
         } else {
@@ -420,7 +428,6 @@ fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long l
             }
         }
 #undef DWTFUSE_BWD_CASE
-#undef DWTFUSE_BWD_WIDE_CASE
     }
 }
 
@@ -428,12 +435,8 @@ namespace {
 
 template <int WAV, int NB>
 const void *bwd_fn(bool alt) {
-    if constexpr (NB > kBwdChunkAlt) {  // shifted-row scenes take chunks of 4
-        return reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
-    } else {
-        return alt ? reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, true>)
-                   : reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
-    }
+    return alt ? reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, true>)
+               : reinterpret_cast<const void *>(&fuse_bwd_kernel<WAV, NB, false>);
 }
 
 template <int WAV>
@@ -473,7 +476,7 @@ BwdArgs make_bwd_args(const float *g, int bands, int64_t H, int64_t W, int wavel
     const bool al16 = (reinterpret_cast<uintptr_t>(g) % 16 == 0) && (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.a4 = (W % 4 == 0) && al16;
     s.alt = (W % 4 == 2) && al16;
-    s.chunk = s.alt ? kBwdChunkAlt : kBwdChunk;
+    s.chunk = kBwdChunk;
     s.ms2 = ms2;
     return s;
 }
@@ -493,7 +496,8 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
     for (int chunk = 0; chunk < max_chunks; ++chunk) {
-        for (int wide = 0; wide < 2; ++wide) {  // scenes whose chunk has 1-4, then 5-8 bands
+        for (int kind = 0; kind < 4; ++kind) {  // (1-4 bands, 5-8 bands) x (Haar, D4)
+            const int wide = kind >> 1, wav = kind & 1;
             std::memset(&t, 0, sizeof t);
             t.R = kDefaultRows;
             int64_t acc = 0;
@@ -502,7 +506,7 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
                 const int b0 = chunk * scenes[i].chunk;
                 const int rest = scenes[i].bands - b0;
                 const int nb = rest < scenes[i].chunk ? rest : scenes[i].chunk;
-                if (nb <= 0 || (nb > 4) != (wide != 0)) continue;
+                if (nb <= 0 || (nb > 4) != (wide != 0) || scenes[i].wavelet != wav) continue;
                 const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
                 t.scenes[k] = scenes[i];
                 t.scenes[k].b0 = b0;
@@ -514,8 +518,11 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
             if (k == 0) continue;
             t.n = k;
             t.item_start[k] = acc;
-            const void *fn = wide ? reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<true>)
-                                  : reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<false>);
+            const void *fns[4] = {reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<false, 0>),
+                                  reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<false, 1>),
+                                  reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<true, 0>),
+                                  reinterpret_cast<const void *>(&fuse_bwd_batched_kernel<true, 1>)};
+            const void *fn = fns[kind];
             const int threads = wide ? kBwdWideThreads : kBwdThreads;
             int occ = 0;
             e = resident_blocks(fn, threads, &occ);
@@ -526,11 +533,9 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
             if (grid == 0) continue;
             e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), stream);
             if (e != cudaSuccess) return e;
-            if (wide)
-                fuse_bwd_batched_kernel<true><<<grid, kBwdWideThreads, 0, stream>>>(t, queue);
-            else
-                fuse_bwd_batched_kernel<false><<<grid, kBwdThreads, 0, stream>>>(t, queue);
-            e = cudaGetLastError();
+            unsigned long long *q = queue;
+            void *args[] = {&t, &q};
+            e = cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, stream);
             if (e != cudaSuccess) return e;
         }
     }
