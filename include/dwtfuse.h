@@ -161,7 +161,10 @@ int dwtfuse_fuse_backward(const float *grad_out, int bands, int64_t H, int64_t W
 size_t dwtfuse_metrics_workspace_size(void);
 
 /* Asynchronous on `stream`: writes four doubles to DEVICE memory out_device:
- * ERGAS, QNR, D_lambda, D_s.  Capturable in a CUDA graph. */
+ * ERGAS, QNR, D_lambda, D_s.  Capturable in a CUDA graph.  On rows off the
+ * 16-byte grid the passes wait on their own bulk copies; a wait that gives up
+ * (about a second; not seen in normal operation) makes all four figures NaN,
+ * and the synchronous dwtfuse_ergas / dwtfuse_qnr return DWTFUSE_ETIMEOUT. */
 int dwtfuse_metrics(const void *fused, int fused_dtype, const void *const *ms, const void *pan,
                     int in_dtype, int bands, int64_t H, int64_t W, int window, void *workspace,
                     size_t ws_bytes, double *out_device, void *stream);
@@ -309,6 +312,17 @@ int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, int rows_pe
  * Process-wide.
  */
 int dwtfuse_set_rows_per_item(int rows);
+
+/*
+ * Test hook for the metric passes' bounded waits (no counterpart in the
+ * paper).  With on = 1, every later metrics call whose PAN-resolution pass
+ * stages unaligned rows (W % 16 != 0, uint8 data) makes one warp post 16 bytes
+ * to its first ring slot that no copy delivers, so that warp's wait gives up
+ * after about a second: the call's figures are NaN and dwtfuse_ergas /
+ * dwtfuse_qnr return DWTFUSE_ETIMEOUT; the context stays usable.  on = 0
+ * (the default) turns it off.  Process-wide; anything else is DWTFUSE_EINVAL.
+ */
+int dwtfuse_set_metric_wait_test(int on);
 
 #ifdef __cplusplus
 }

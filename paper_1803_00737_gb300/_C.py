@@ -80,6 +80,7 @@ _SIGS = {
     "dwtfuse_fuse_batched": (_i, [ctypes.POINTER(Scene), _i, _vp, _sz, _i, _i, _vp]),
     "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
     "dwtfuse_set_rows_per_item": (_i, [_i]),
+    "dwtfuse_set_metric_wait_test": (_i, [_i]),
     "dwtfuse_fuse_batched_noalloc": (_i, [ctypes.POINTER(Scene), _i, _i, _i, _vp]),
     "dwtfuse_metrics_workspace_size": (_sz, []),
     "dwtfuse_metrics": (_i, [_vp, _i, ctypes.POINTER(_vp), _vp, _i, _i, _i64, _i64, _i, _vp, _sz,
@@ -406,3 +407,8 @@ def dwtfuse_get_last_device_status(workspace: torch.Tensor, stream=None) -> int:
 
 def dwtfuse_set_rows_per_item(rows: int) -> None:
     _check(lib().dwtfuse_set_rows_per_item(int(rows)), "dwtfuse_set_rows_per_item")
+
+
+def dwtfuse_set_metric_wait_test(on: bool) -> None:
+    """Test hook: make the unaligned metric pass's bounded wait give up (see dwtfuse.h)."""
+    _check(lib().dwtfuse_set_metric_wait_test(int(bool(on))), "dwtfuse_set_metric_wait_test")

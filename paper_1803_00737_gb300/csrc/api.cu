@@ -18,6 +18,7 @@ std::unordered_map<const void *, int> g_occ;
 std::map<std::pair<int, const void *>, int> g_occ_smem;
 std::unordered_map<int, int> g_sms;
 std::atomic<int> g_rows{0};  // 0: balanced_rows() per launch
+std::atomic<int> g_metric_wait_test{0};  // dwtfuse_set_metric_wait_test
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 }  // namespace
 
@@ -211,6 +212,12 @@ int dwtfuse_version(void) { return 100; }
 
 int dwtfuse_last_cuda_error(void) { return (int)g_last_cuda; }
 
+int dwtfuse_set_metric_wait_test(int on) {
+    if (on != 0 && on != 1) return DWTFUSE_EINVAL;
+    g_metric_wait_test.store(on, std::memory_order_relaxed);
+    return DWTFUSE_OK;
+}
+
 int dwtfuse_set_rows_per_item(int rows) {
     if (rows < 0 || rows > 4096) return DWTFUSE_EINVAL;
     g_rows.store(rows, std::memory_order_relaxed);
@@ -362,6 +369,7 @@ static int make_metrics(const void *fused, int fused_dtype, const void *const *m
     m->a16 = a16;
     m->a32_ms = a32;
     m->workspace = static_cast<double *>(workspace);
+    m->wait_test = g_metric_wait_test.load(std::memory_order_relaxed);
     return DWTFUSE_OK;
 }
 
@@ -445,10 +453,15 @@ int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int6
 
 static int metrics_to_host(const MetricLaunch &m, void *stream, double *out4) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double r[kMetricStatusSlot + 1];
     cudaError_t e = launch_metrics(m, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out4, m.workspace, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, m.workspace, sizeof r, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < 4; ++k) out4[k] = r[k];
+    int status;
+    std::memcpy(&status, &r[kMetricStatusSlot], sizeof status);
+    return status == DWTFUSE_ETIMEOUT ? DWTFUSE_ETIMEOUT : DWTFUSE_OK;
 }
 
 int dwtfuse_ergas(const void *fused, int fused_dtype, const void *const *ms, int in_dtype,

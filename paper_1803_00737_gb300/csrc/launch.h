@@ -53,6 +53,7 @@ struct MetricLaunch {
                         // their count at kMetricPanCtasSlot
     int32_t ms_early;   // the kernel just before on the stream is one of ours that writes none of
                         // the MS pass's inputs: the MS pass may start as it drains (see launch_metrics)
+    int32_t wait_test;  // dwtfuse_set_metric_wait_test: one warp's first slot waits on bytes never sent
 };
 
 // Fused forward + PAN-resolution metrics (fuse_metrics.cu): uint8 inputs, a
@@ -116,6 +117,7 @@ cudaError_t launch_fuse_metrics(const SceneArgs &s, double *pan_partial, int str
 // Metrics workspace: doubles [0, 4) results, the int at double 4 the count of
 // PAN-resolution partial rows written by the fused kernel, rows from double 8.
 constexpr int64_t kMetricPanCtasSlot = 4;
+constexpr int64_t kMetricStatusSlot = 5;  // int: DWTFUSE_OK, or DWTFUSE_ETIMEOUT when a bounded wait gave up
 constexpr int64_t kMetricPanPartialOffset = 8;
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);

@@ -182,7 +182,7 @@ struct MetricArgs {
     int32_t want_q;
     int32_t a4_fused, a4_in;       // 4-pixel vector path allowed
     int32_t stride;                // doubles per CTA partial row
-    int32_t pad_;
+    int32_t wait_test;             // PAN pass, unaligned rows: warp 0 of CTA 0 posts 16 bytes never sent
 };
 
 // --------------------------------------------------------------- PAN-resolution pass
@@ -538,6 +538,7 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     int64_t pl_n = 0;
     int kind = 0, dst_off = 0;  // kind 1: PAN-resolution row, 2: MS row
     bool err = false;
+    bool stall = GEN && a.wait_test && blockIdx.x == 0 && warp == 0;  // test hook, first slot only
     if (GEN) {
         br.init(reinterpret_cast<uint64_t *>(smem + C::kBarOffset) + warp * S, lane);
         if (lane < NB) {
@@ -570,6 +571,10 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
                     else if (kind == 2)
                         stage_row(slot + dst_off, pl + (y >> 1) * W2 + (x0 >> 1), span / 2, pl, pl + pl_n,
                                   br.bar + br.issue_slot);
+                    if (stall) {
+                        if (lane == 0) mbar_expect_tx(br.bar + br.issue_slot, 16u);
+                        stall = false;
+                    }
                     br.commit(lane);
                 }
                 return;
@@ -1165,10 +1170,13 @@ metrics_finalize_kernel(const double *pan_part, const double *ms_part, int ctas_
         ds += __shfl_xor_sync(0xffffffffu, ds, o);
     }
     if (lane != 0) return;
+    int *status = reinterpret_cast<int *>(out + kMetricStatusSlot);
     if (tot_pan[P + nb] + tot_ms[P + nb] > 0.0) {
         out[0] = out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
+        *status = DWTFUSE_ETIMEOUT;
         return;
     }
+    *status = DWTFUSE_OK;
     out[0] = 100.0 * 0.5 * sqrt(e / nb);
     if (!q_ok) {
         out[1] = out[2] = out[3] = __longlong_as_double(0x7ff8000000000000ll);
@@ -1292,6 +1300,7 @@ cudaError_t launch_metrics(const MetricLaunch &m, cudaStream_t stream) {
     a.a4_fused = m.a4_fused;
     a.a4_in = m.a4_in;
     a.stride = kMetricStride;
+    a.wait_test = m.wait_test;
     const bool fast = !m.fused_f32 && !m.in_f32;
     double *out = m.workspace;
     double *pan_part = m.workspace + kMetricPanPartialOffset;

@@ -145,6 +145,12 @@ def test_batched_backward_validation(L):
     assert call() == _C.EALIGN
 
 
+def test_metric_wait_test_hook_validation(L):
+    assert L.dwtfuse_set_metric_wait_test(2) == _C.EINVAL
+    assert L.dwtfuse_set_metric_wait_test(-1) == _C.EINVAL
+    assert L.dwtfuse_set_metric_wait_test(0) == _C.OK
+
+
 def test_rows_knob(L):
     assert L.dwtfuse_set_rows_per_item(-1) == _C.EINVAL
     assert L.dwtfuse_set_rows_per_item(16) == _C.OK

@@ -181,3 +181,29 @@ def test_config1_metrics_full_size(ws):
     got = gpu_metrics(u8, ms, pan, ws)
     ref = ref_metrics(u8, ms, pan)
     check(got, ref, False)
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(ws):
+    """Rows off the 16-byte grid are staged by bulk copies whose mbarrier waits
+    are bounded.  With the test hook one warp waits on 16 bytes that no copy
+    sends: after about a second the call reports DWTFUSE_ETIMEOUT (the async
+    form NaN figures), and the next call on the same context is exact again."""
+    H, W, B = 64, 534, 3  # W % 16 != 0: the staged path
+    pan, ms = scenegen.make_scene(H, W, B, seed=12, device=DEV)
+    u8 = torch.empty((B, H, W), dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_fuse(pan, ms, 1, None, u8)
+    ref = _C.dwtfuse_ergas(u8, ms, ws)
+    _C.dwtfuse_set_metric_wait_test(True)
+    try:
+        with pytest.raises(_C.DwtfuseError) as err:
+            _C.dwtfuse_ergas(u8, ms, ws)
+        assert err.value.status == _C.ETIMEOUT
+        out = torch.zeros(4, dtype=torch.float64, device=DEV)
+        _C.dwtfuse_metrics(u8, ms, pan, ws, out)
+        torch.cuda.synchronize()
+        assert torch.isnan(out).all()
+    finally:
+        _C.dwtfuse_set_metric_wait_test(False)
+    assert _C.dwtfuse_ergas(u8, ms, ws) == ref
+    got = gpu_metrics(u8, ms, pan, ws)
+    check(got, ref_metrics(u8, ms, pan), False)
