@@ -52,8 +52,8 @@ struct BwdArgs {
     int32_t ms2;                  // W/2 even and every gms 8-byte aligned: pair stores
     int32_t alt;                  // W % 4 == 2 with 16-byte aligned g / gpan: shifted odd rows
     int32_t wavelet;              // 0 Haar, 1 D4
-    int32_t chunk;                // bands per launch
     int32_t b0;                   // first band of the chunk (batched tables)
+    int32_t pad_;
 };
 
 // Scene table of one launch of the batched backward (band chunk b0 of n scenes).
@@ -476,7 +476,6 @@ BwdArgs make_bwd_args(const float *g, int bands, int64_t H, int64_t W, int wavel
     const bool al16 = (reinterpret_cast<uintptr_t>(g) % 16 == 0) && (reinterpret_cast<uintptr_t>(gpan) % 16 == 0);
     s.a4 = (W % 4 == 0) && al16;
     s.alt = (W % 4 == 2) && al16;
-    s.chunk = kBwdChunk;
     s.ms2 = ms2;
     return s;
 }
@@ -489,7 +488,7 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
     for (int i = 0; i < n; ++i) {
         scenes[i] = make_bwd_args(in[i].grad_out, in[i].bands, in[i].H, in[i].W, in[i].wavelet, in[i].grad_pan,
                                   in[i].grad_ms);
-        const int nc = (scenes[i].bands + scenes[i].chunk - 1) / scenes[i].chunk;
+        const int nc = (scenes[i].bands + kBwdChunk - 1) / kBwdChunk;
         max_chunks = nc > max_chunks ? nc : max_chunks;
     }
     int sms = 0;
@@ -503,9 +502,9 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
             int64_t acc = 0;
             int k = 0;
             for (int i = 0; i < n; ++i) {
-                const int b0 = chunk * scenes[i].chunk;
+                const int b0 = chunk * kBwdChunk;
                 const int rest = scenes[i].bands - b0;
-                const int nb = rest < scenes[i].chunk ? rest : scenes[i].chunk;
+                const int nb = rest < kBwdChunk ? rest : kBwdChunk;
                 if (nb <= 0 || (nb > 4) != (wide != 0) || scenes[i].wavelet != wav) continue;
                 const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
                 t.scenes[k] = scenes[i];
@@ -548,8 +547,8 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    for (int b0 = 0; b0 < bands; b0 += s.chunk) {
-        const int nb = bands - b0 < s.chunk ? bands - b0 : s.chunk;
+    for (int b0 = 0; b0 < bands; b0 += kBwdChunk) {
+        const int nb = bands - b0 < kBwdChunk ? bands - b0 : kBwdChunk;
         const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb, s.alt != 0) : bwd_fn_nb<1>(nb, s.alt != 0);
         const int threads = bwd_threads(nb), warps = threads / 32;
         int occ = 0;
