@@ -15,6 +15,10 @@
 // Same warp strips as the fused kernels: a lane owns image columns x..x+3
 // (coefficient columns n, n+1 of each half) and walks down R coefficient rows
 // with a sliding window of image rows (forward) or coefficient rows (inverse).
+// Haar loads two coefficient rows' inputs per step (16384^2: forward 0.32 ->
+// 0.23 ms, inverse 0.37 -> 0.35 ms; the forward only with streaming stores,
+// with plain stores the two-row body came out slower, 0.46 ms); the same for
+// D4 measured slower (forward 0.29 -> 0.37 ms), so D4 keeps one row per step.
 #include "fuse_tile.cuh"
 #include "launch.h"
 
@@ -37,10 +41,10 @@ struct DwtArgs {
 // Two coefficients (columns n, n+1) of one coefficient row; n+1 only if `two`.
 __device__ __forceinline__ void store_pair(float *p, bool pair, bool two, float a, float b) {
     if (pair) {
-        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(a, b));
     } else {
-        p[0] = a;
-        if (two) p[1] = b;
+        __stcs(p, a);
+        if (two) __stcs(p + 1, b);
     }
 }
 
@@ -62,11 +66,7 @@ __device__ __forceinline__ void dwt2_item(const DwtArgs &s, int64_t x0, int64_t 
     const T *img = static_cast<const T *>(s.src);
     float *Z = s.dst_f32;
     if (WAV == 0) {
-        for (int64_t m = m_s; m < m_e; ++m) {
-            float p0[4], p1[4];
-            load_row4(img + (2 * m) * W, c, a4, p0);
-            load_row4(img + (2 * m + 1) * W, c, a4, p1);
-            if (!c.active) continue;
+        auto emit = [&](int64_t m, const float *p0, const float *p1) {
             float A0[2], D0[2], A1[2], D1[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {  // Eq. 1-2 along the rows
@@ -80,6 +80,19 @@ __device__ __forceinline__ void dwt2_item(const DwtArgs &s, int64_t x0, int64_t 
             store_pair(Z + m * W + W2 + c.nB, pair, c.two, (D0[0] + D1[0]) * 0.5f, (D0[1] + D1[1]) * 0.5f);
             store_pair(Z + (H2 + m) * W + c.nB, pair, c.two, (A0[0] - A1[0]) * 0.5f, (A0[1] - A1[1]) * 0.5f);
             store_pair(Z + (H2 + m) * W + W2 + c.nB, pair, c.two, (D0[0] - D1[0]) * 0.5f, (D0[1] - D1[1]) * 0.5f);
+        };
+        for (int64_t m = m_s; m < m_e; m += 2) {  // two coefficient rows' image rows in flight
+            const bool second = m + 1 < m_e;
+            float p0[4], p1[4], p2[4], p3[4];
+            load_row4(img + (2 * m) * W, c, a4, p0);
+            load_row4(img + (2 * m + 1) * W, c, a4, p1);
+            if (second) {
+                load_row4(img + (2 * m + 2) * W, c, a4, p2);
+                load_row4(img + (2 * m + 3) * W, c, a4, p3);
+            }
+            if (!c.active) continue;
+            emit(m, p0, p1);
+            if (second) emit(m + 1, p2, p3);
         }
         return;
     }
@@ -148,13 +161,13 @@ __device__ __forceinline__ void idwt2_item(const DwtArgs &s, int64_t x0, int64_t
     OutPtrs o{s.dst_f32, s.dst_u8};
     (void)HW;
     if (WAV == 0) {
-        for (int64_t m = m_s; m < m_e; ++m) {
-            float ll[2], hl[2], lh[2], hh[2];
+        auto ld = [&](int64_t m, float *ll, float *hl, float *lh, float *hh) {
             ll[0] = __ldg(Z + m * W + c.nB);              ll[1] = __ldg(Z + m * W + c.nC);
             hl[0] = __ldg(Z + m * W + W2 + c.nB);         hl[1] = __ldg(Z + m * W + W2 + c.nC);
             lh[0] = __ldg(Z + (H2 + m) * W + c.nB);       lh[1] = __ldg(Z + (H2 + m) * W + c.nC);
             hh[0] = __ldg(Z + (H2 + m) * W + W2 + c.nB);  hh[1] = __ldg(Z + (H2 + m) * W + W2 + c.nC);
-            if (!c.active) continue;
+        };
+        auto emit = [&](int64_t m, const float *ll, const float *hl, const float *lh, const float *hh) {
             // Eq. 11-12 on the columns, then on the rows
             float v0[4], v1[4];
 #pragma unroll
@@ -168,6 +181,15 @@ __device__ __forceinline__ void idwt2_item(const DwtArgs &s, int64_t x0, int64_t
             }
             store4(o, (2 * m) * W + c.x, a4, c.two, v0);
             store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+        };
+        for (int64_t m = m_s; m < m_e; m += 2) {  // two coefficient rows in flight
+            const bool second = m + 1 < m_e;
+            float ll[2], hl[2], lh[2], hh[2], ll2[2], hl2[2], lh2[2], hh2[2];
+            ld(m, ll, hl, lh, hh);
+            if (second) ld(m + 1, ll2, hl2, lh2, hh2);
+            if (!c.active) continue;
+            emit(m, ll, hl, lh, hh);
+            if (second) emit(m + 1, ll2, hl2, lh2, hh2);
         }
         return;
     }
