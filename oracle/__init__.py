@@ -46,12 +46,20 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+# A prebuilt oracle library to load instead of liboracle.so.  Only the
+# mutation tests set it, to run the pins against a copy of dwt_oracle.c with a
+# planted mistake.
+_LIB_ENV = "DWTFUSE_ORACLE_LIB"
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+            path = os.environ.get(_LIB_ENV)
+            if not path:
+                path = build()
+            lib = ctypes.CDLL(path)
             i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
             sig = {
                 "oracle_d4_h": (None, [_D]),

@@ -190,6 +190,10 @@ def test_point_evaluator_matches_whole_image(wav):
     ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
     pts = O.fuse_points(pan, ms, wav, ys.ravel(), xs.ravel())
     np.testing.assert_array_equal(pts, F.ravel())
+    # the same from float inputs (the evaluator's other input path)
+    pf, mf = RNG.uniform(0, 255, (H, W)), RNG.uniform(0, 255, (H // 2, W // 2))
+    np.testing.assert_allclose(O.fuse_points(pf, mf, wav, ys.ravel(), xs.ravel()),
+                               O.fuse(pf, [mf], wav)[0].ravel(), rtol=0, atol=1e-10)
 
 
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
@@ -358,3 +362,40 @@ def test_qnr_spatial_term_closed_form():
                 qs.append((2 * a / (1 + a * a)) * (2 * mx * my / (mx * mx + my * my)))
         terms.append(abs(np.mean(qs) - 1.0))
     assert abs(ds - np.mean(terms)) < 1e-12
+
+
+def test_qnr_spectral_term_and_product_closed_form():
+    """Every band affine in one base image X: F_l = a_l X + b_l at PAN size,
+    MS_l = c_l X~ + d_l at MS size (X~ the 2x2 block mean of X), PAN = X.  For
+    y = p x + q and z = r x + s on a window of x with mean m, Q(y, z) =
+    [2pr / (p^2 + r^2)] [2 mu_y mu_z / (mu_y^2 + mu_z^2)], mu = p m + q, r m + s;
+    so D_lambda (mean over ordered pairs), D_s and QNR = (1 - D_lambda)(1 - D_s)
+    all follow from the window means of X and X~, with both terms nonzero."""
+    H = W = 128
+    x = RNG.uniform(10, 250, (H, W))
+    x_lo = x.reshape(H // 2, 2, W // 2, 2).mean(axis=(1, 3))
+    fab = [(1.0, 0.0), (0.8, 10.0), (1.25, -5.0)]
+    mcd = [(1.0, 2.0), (0.9, 0.0), (1.1, 4.0)]
+    fused = np.stack([a * x + b for a, b in fab])
+    ms = [c * x_lo + d for c, d in mcd]
+    q, dl, ds = O.qnr(fused, ms, x)
+
+    def win_means(img):
+        n = img.shape[0] // 32, img.shape[1] // 32
+        return [img[32 * i:32 * i + 32, 32 * j:32 * j + 32].mean() for i in range(n[0]) for j in range(n[1])]
+
+    def q_aff(means, p, qq, r, s):
+        out = []
+        for m in means:
+            mu_y, mu_z = p * m + qq, r * m + s
+            out.append((2 * p * r / (p * p + r * r)) * (2 * mu_y * mu_z / (mu_y ** 2 + mu_z ** 2)))
+        return np.mean(out)
+
+    mh, ml = win_means(x), win_means(x_lo)
+    B = len(fab)
+    dl_ref = np.mean([abs(q_aff(mh, *fab[l], *fab[r]) - q_aff(ml, *mcd[l], *mcd[r]))
+                      for l in range(B) for r in range(B) if l != r])
+    ds_ref = np.mean([abs(q_aff(mh, *fab[l], 1.0, 0.0) - q_aff(ml, *mcd[l], 1.0, 0.0)) for l in range(B)])
+    assert dl_ref > 1e-4 and ds_ref > 1e-4
+    assert abs(dl - dl_ref) < 1e-12 and abs(ds - ds_ref) < 1e-12
+    assert abs(q - (1.0 - dl_ref) * (1.0 - ds_ref)) < 1e-12
