@@ -241,13 +241,17 @@ typedef struct {
 } dwtfuse_grad_scene;
 
 /*
- * Batched adjoint: dwtfuse_fuse_backward for up to DWTFUSE_MAX_SCENES scenes
- * of any legal sizes, as one persistent launch per chunk of 4 bands (the
- * second and later chunks add into grad_pan, so they follow in order).
- * Arguments, layouts and errors per scene as dwtfuse_fuse_backward; the
- * workspace is dwtfuse_batched_workspace_size() bytes of device memory, 16-byte
- * aligned, scratch between calls (calls sharing it must not overlap).
- * Asynchronous on `stream`; the scene array is read before the call returns.
+ * Batched adjoint: dwtfuse_fuse_backward (the transpose of the Sec. 2 fusion,
+ * formulas above) for up to DWTFUSE_MAX_SCENES scenes of any legal sizes,
+ * band counts and wavelets.  Per chunk of 8 bands, one persistent launch for
+ * each wavelet and chunk width present (1-4 or 5-8 bands); the second and
+ * later chunks add into grad_pan, so they follow in order.  Results equal
+ * dwtfuse_fuse_backward per scene bit for bit.  Arguments, layouts and errors
+ * per scene as dwtfuse_fuse_backward; more than DWTFUSE_MAX_SCENES scenes is
+ * DWTFUSE_ESHAPE.  The workspace is dwtfuse_batched_workspace_size() bytes of
+ * device memory, 16-byte aligned, scratch between calls (calls sharing it must
+ * not overlap).  Asynchronous on `stream`, capturable in a CUDA graph; the
+ * scene array is read before the call returns.
  */
 int dwtfuse_fuse_backward_batched(const dwtfuse_grad_scene *scenes, int n, void *workspace,
                                   size_t ws_bytes, void *stream);
