@@ -753,10 +753,15 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     }
 }
 
+// MS-resolution pass: up to 6 bands, 8-warp CTAs, two per SM (the half of an
+// SM that the fused forward's first finished CTA frees is enough for one, so
+// as a programmatic dependent it starts in that kernel's tail: 16384^2 x 6
+// step 1.687 -> 1.650 ms against 16-warp CTAs).
 template <int NB, bool GEN>
 struct FastMs {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
-    static constexpr int kWarps = NB <= 6 ? 16 : (GEN ? kGenWarps : 8);
+    static constexpr int kWarps = NB <= 6 ? 8 : (GEN ? kGenWarps : 8);
+    static constexpr int kMinBlocks = NB <= 6 ? 2 : 1;
     static constexpr int kFastWarps = kWarps;
     static constexpr int kStages = NB <= 6 || GEN ? 2 : 3;
     static constexpr int kPanRow = 2 * kStrip + 32;  // 32 PAN pixels per lane
@@ -783,7 +788,7 @@ __device__ __forceinline__ int dp4a_su(int a, uint32_t b, int c) {
 // on the GEN path lane b stages MS band b's row and lanes NB, NB + 1 the two
 // PAN rows above it.
 template <int NB, bool GEN>
-__global__ void __launch_bounds__(FastMs<NB, GEN>::kWarps * 32, 1)
+__global__ void __launch_bounds__(FastMs<NB, GEN>::kWarps * 32, FastMs<NB, GEN>::kMinBlocks)
 metrics_ms_u8_kernel(const __grid_constant__ MetricArgs a) {
     using C = FastMs<NB, GEN>;
     constexpr int kFastWarps = C::kWarps;
