@@ -152,6 +152,17 @@ def _stream(stream) -> int:
     return int(stream)
 
 
+def _need(t: torch.Tensor | None, n: int, dtype: torch.dtype | None, name: str) -> None:
+    """The library reads or writes n elements of t's dtype at t's address: refuse
+    a smaller buffer or another element type (it would run past the buffer)."""
+    if t is None:
+        return
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {n}")
+
+
 def _bands(ms) -> list[torch.Tensor]:
     if isinstance(ms, torch.Tensor):
         return [ms[b] for b in range(ms.shape[0])] if ms.dim() == 3 else [ms]
@@ -184,6 +195,10 @@ def dwtfuse_fuse_ex(pan: torch.Tensor, ms, wavelet: int, ll_gain: float,
     """dwtfuse_fuse with an explicit LL replacement gain."""
     bands = _bands(ms)
     H, W = pan.shape
+    for b, m in enumerate(bands):
+        _need(m, (H // 2) * (W // 2), pan.dtype, f"ms[{b}]")
+    _need(out_f32, len(bands) * H * W, torch.float32, "out_f32")
+    _need(out_u8, len(bands) * H * W, torch.uint8, "out_u8")
     ptrs = (_vp * len(bands))(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
     st = lib().dwtfuse_fuse_ex(_dev(pan, "pan"), ptrs, len(bands), H, W, int(wavelet),
                                _dtype_code(pan, "pan"), float(ll_gain),
@@ -208,6 +223,8 @@ def dwtfuse_idwt2(coeffs: torch.Tensor, wavelet: int, out_f32: torch.Tensor | No
     H, W = coeffs.shape
     if coeffs.dtype != torch.float32:
         raise TypeError("coeffs must be float32")
+    _need(out_f32, H * W, torch.float32, "out_f32")
+    _need(out_u8, H * W, torch.uint8, "out_u8")
     _check(lib().dwtfuse_idwt2(_dev(coeffs, "coeffs"), H, W, int(wavelet),
                                _dev(out_f32, "out_f32") if out_f32 is not None else None,
                                _dev(out_u8, "out_u8") if out_u8 is not None else None,
@@ -223,6 +240,9 @@ def dwtfuse_fuse_backward(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.
     gms = _bands(grad_ms)
     if len(gms) != B:
         raise ValueError("one grad_ms buffer per band")
+    _need(grad_pan, H * W, torch.float32, "grad_pan")
+    for b, g in enumerate(gms):
+        _need(g, (H // 2) * (W // 2), torch.float32, f"grad_ms[{b}]")
     ptrs = (_vp * B)(*[_dev(g, f"grad_ms[{b}]") for b, g in enumerate(gms)])
     st = lib().dwtfuse_fuse_backward(_dev(grad_out, "grad_out"), B, H, W, int(wavelet),
                                      _dev(grad_pan, "grad_pan"), ptrs, _stream(stream))
@@ -236,6 +256,9 @@ def make_grad_scene(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.Tensor
     gms = _bands(grad_ms)
     if len(gms) != B:
         raise ValueError("one grad_ms buffer per band")
+    _need(grad_pan, H * W, torch.float32, "grad_pan")
+    for b, g in enumerate(gms):
+        _need(g, (H // 2) * (W // 2), torch.float32, f"grad_ms[{b}]")
     s = GradScene()
     s.grad_out = _dev(grad_out, "grad_out")
     s.grad_pan = _dev(grad_pan, "grad_pan")
@@ -246,7 +269,8 @@ def make_grad_scene(grad_out: torch.Tensor, wavelet: int, grad_pan: torch.Tensor
 
 
 def dwtfuse_fuse_backward_batched(scenes: list[GradScene], workspace: torch.Tensor, stream=None) -> None:
-    """The adjoint of every scene in one persistent launch per chunk of 4 bands."""
+    """The adjoint of every scene: per chunk of 8 bands, one persistent launch per
+    wavelet and chunk width (see dwtfuse.h)."""
     arr = (GradScene * len(scenes))(*scenes)
     st = lib().dwtfuse_fuse_backward_batched(arr, len(scenes), _dev(workspace, "workspace"),
                                              workspace.numel() * workspace.element_size(),
@@ -261,6 +285,11 @@ def dwtfuse_batched_workspace_size() -> int:
 def make_scene(pan: torch.Tensor, ms, wavelet: int, out_f32: torch.Tensor | None,
                out_u8: torch.Tensor | None = None) -> Scene:
     bands = _bands(ms)
+    H, W = pan.shape
+    for b, m in enumerate(bands):
+        _need(m, (H // 2) * (W // 2), pan.dtype, f"ms[{b}]")
+    _need(out_f32, len(bands) * H * W, torch.float32, "out_f32")
+    _need(out_u8, len(bands) * H * W, torch.uint8, "out_u8")
     s = Scene()
     s.pan = _dev(pan, "pan")
     for b, m in enumerate(bands):
@@ -304,6 +333,8 @@ def _metric_args(fused: torch.Tensor, ms):
     B, H, W = fused.shape
     if len(bands) != B:
         raise ValueError("one MS band per fused band")
+    for b, m in enumerate(bands):
+        _need(m, (H // 2) * (W // 2), bands[0].dtype, f"ms[{b}]")
     ptrs = (_vp * B)(*[_dev(m, f"ms[{b}]") for b, m in enumerate(bands)])
     return bands, B, H, W, ptrs
 
@@ -314,6 +345,7 @@ def dwtfuse_metrics(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch
     bands, B, H, W, ptrs = _metric_args(fused, ms)
     if out_device.dtype != torch.float64 or out_device.numel() < 4:
         raise ValueError("out_device must be a float64 CUDA tensor with >= 4 elements")
+    _need(pan, H * W, bands[0].dtype, "pan")
     st = lib().dwtfuse_metrics(_dev(fused, "fused"), _dtype_code(fused, "fused"), ptrs,
                                _dev(pan, "pan"), _dtype_code(pan, "pan"), B, H, W, int(window),
                                _dev(workspace, "workspace"), workspace.numel() * workspace.element_size(),
@@ -392,6 +424,7 @@ def dwtfuse_ergas(fused: torch.Tensor, ms, workspace: torch.Tensor, stream=None)
 def dwtfuse_qnr(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch.Tensor,
                 window: int = 32, stream=None) -> tuple[float, float, float]:
     bands, B, H, W, ptrs = _metric_args(fused, ms)
+    _need(pan, H * W, bands[0].dtype, "pan")
     q, dl, ds = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     st = lib().dwtfuse_qnr(_dev(fused, "fused"), _dtype_code(fused, "fused"), ptrs, _dev(pan, "pan"),
                            _dtype_code(pan, "pan"), B, H, W, int(window), _dev(workspace, "workspace"),

@@ -163,3 +163,43 @@ def test_cpu_tensors_are_rejected():
     ms = torch.zeros((1, 2, 2), dtype=torch.uint8)
     with pytest.raises(ValueError, match="CUDA"):
         _C.dwtfuse_fuse(pan, ms, 0, torch.zeros((1, 4, 4)), None)
+
+
+def test_binding_refuses_buffers_the_call_would_overrun():
+    """The binding checks every buffer the library reads or writes against the
+    element count and type the call implies, before any pointer reaches C;
+    right-sized CPU tensors get as far as the CUDA check."""
+    torch = pytest.importorskip("torch")
+    H, W, B = 8, 12, 3
+    pan = torch.zeros((H, W), dtype=torch.uint8)
+    ms = torch.zeros((B, H // 2, W // 2), dtype=torch.uint8)
+    f32 = torch.zeros((B, H, W))
+    u8 = torch.zeros((B, H, W), dtype=torch.uint8)
+    g = torch.zeros((B, H, W))
+    gp = torch.zeros((H, W))
+    gm = torch.zeros((B, H // 2, W // 2))
+    ok = [
+        lambda: _C.make_scene(pan, ms, 1, f32, u8),
+        lambda: _C.dwtfuse_fuse_ex(pan, ms, 1, 2.0, f32, u8),
+        lambda: _C.make_grad_scene(g, 1, gp, gm),
+        lambda: _C.dwtfuse_fuse_backward(g, 1, gp, gm),
+        lambda: _C.dwtfuse_idwt2(gp, 1, gp.clone(), None),
+    ]
+    for call in ok:
+        with pytest.raises(ValueError, match="CUDA"):
+            call()
+    short = [
+        lambda: _C.make_scene(pan, ms, 1, f32[:2], None),
+        lambda: _C.make_scene(pan, ms[:, :2], 1, None, u8),
+        lambda: _C.dwtfuse_fuse_ex(pan, ms, 1, 2.0, None, u8[:, :4]),
+        lambda: _C.make_grad_scene(g, 1, gp[:4], gm),
+        lambda: _C.dwtfuse_fuse_backward(g, 1, gp, gm[:, :2]),
+        lambda: _C.dwtfuse_idwt2(gp, 1, None, torch.zeros((H, W // 2), dtype=torch.uint8)),
+    ]
+    for call in short:
+        with pytest.raises(ValueError, match="holds"):
+            call()
+    with pytest.raises(TypeError):
+        _C.make_scene(pan, ms, 1, u8, None)  # a uint8 buffer as the float32 output
+    with pytest.raises(TypeError):
+        _C.dwtfuse_fuse_backward(g, 1, gp, gm.double())
