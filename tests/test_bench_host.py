@@ -76,3 +76,14 @@ def test_gpu_arm_helpers_are_defined():
     import builtins
     missing = [n for n in called if not hasattr(bench, n) and not hasattr(builtins, n)]
     assert not missing, missing
+
+
+def test_dram_traffic_record_matches_the_kernel_sources():
+    """The roofline's `traffic` comes from an ncu capture of the forward-and-
+    score kernel, keyed by a hash of its sources; a change to those sources
+    must come with a new capture (else the JSON line reports null)."""
+    import bench
+    assert bench.kernel_hash() in bench.KNOWN_TRAFFIC
+    t = bench.KNOWN_TRAFFIC[bench.kernel_hash()]
+    alg = bench.fwd_bytes_per_launch()
+    assert 0.95 * alg <= t <= 1.05 * alg  # DRAM bytes per launch near the algorithmic bytes
