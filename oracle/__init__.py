@@ -75,6 +75,8 @@ def _load():
                 "oracle_fuse": (i, [i, l, l, i, d, _D, ctypes.POINTER(_D), _D]),
                 "oracle_fuse_adjoint": (i, [i, l, l, i, d, _D, _D, ctypes.POINTER(_D)]),
                 "oracle_fuse_points": (i, [i, l, l, d, _D, _U8, _D, _U8, l, _L, _L, _D]),
+                "oracle_fuse_adjoint_points": (i, [i, l, l, i, d, _D, l, l, l, l, l, _L, _L, _D,
+                                                   l, _L, _L, _D]),
                 "oracle_to_u8": (None, [l, _D, _U8]),
                 "oracle_dwt2_points": (i, [i, l, l, _D, _U8, l, _L, _L, _D]),
                 "oracle_ergas_t": (d, [l, l, i, _V, i, ctypes.POINTER(_V), i]),
@@ -241,6 +243,39 @@ def fuse_points(pan, ms_band, wavelet: int, ys, xs, gain: float | None = None) -
                                       ys.size, ys.ctypes.data_as(_L), xs.ctypes.data_as(_L),
                                       _p(out)), "fuse_points")
     return out
+
+
+def fuse_adjoint_points(g_win, wavelet: int, H: int, W: int, ys=(), xs=(), is_=(), js=(),
+                        gy0: int = 0, gx0: int = 0, gain: float | None = None):
+    """The transposed fusion (fuse_adjoint) evaluated lazily at sampled outputs.
+
+    g_win (B, hg, wg): the output gradient of every band on a periodic window of
+    the H x W image, g_win[b, r, s] = grad_out[b, (gy0 + r) % H, (gx0 + s) % W]
+    (the whole gradient with gy0 = gx0 = 0).  Returns (grad_pan at (ys[k], xs[k]),
+    grad_ms (B, len(is_)) at MS pixels (is_[k], js[k])).  Raises if a value needs
+    gradient outside the window."""
+    g = _f64(g_win)
+    if g.ndim != 3 or g.shape[1] > H or g.shape[2] > W:
+        raise ValueError("g_win must be (B, hg <= H, wg <= W)")
+    B, hg, wg = g.shape
+    gn = default_gain(wavelet) if gain is None else float(gain)
+    ys, xs = (np.ascontiguousarray(a, dtype=np.int64) for a in (ys, xs))
+    is_, js = (np.ascontiguousarray(a, dtype=np.int64) for a in (is_, js))
+    if ys.shape != xs.shape or is_.shape != js.shape or ys.ndim != 1 or is_.ndim != 1:
+        raise ValueError("coordinates must be equal-length 1D arrays")
+    if ys.size and (ys.min() < 0 or ys.max() >= H or xs.min() < 0 or xs.max() >= W):
+        raise ValueError("PAN sample outside the image")
+    if is_.size and (is_.min() < 0 or is_.max() >= H // 2 or js.min() < 0 or js.max() >= W // 2):
+        raise ValueError("MS sample outside the image")
+    gp = np.empty(ys.size)
+    gm = np.empty((B, is_.size))
+    _check(_load().oracle_fuse_adjoint_points(
+        int(wavelet), int(H), int(W), B, ctypes.c_double(gn), _p(g), int(gy0) % H, int(gx0) % W, hg, wg,
+        ys.size, ys.ctypes.data_as(_L), xs.ctypes.data_as(_L), _p(gp),
+        is_.size, is_.ctypes.data_as(_L), js.ctypes.data_as(_L), _p(gm)), "fuse_adjoint_points")
+    if np.isnan(gp).any() or np.isnan(gm).any():
+        raise ValueError("a sample needs output gradient outside the given window")
+    return gp, gm
 
 
 def dwt2_points(img, wavelet: int, is_, js) -> np.ndarray:

@@ -455,6 +455,144 @@ int oracle_dwt2_points(int kind, long H, long W, const double *img, const uint8_
     return 0;
 }
 
+/* ------------------------------------- point-wise evaluation of the adjoint */
+
+/* Users of input index i under a 1D map: the outputs o whose tap list names i,
+ * each with the summed weight of those taps.  The transposed map at i is
+ * sum over users (o, w) of w * ybar[o].  Each output of the forward map reads
+ * inputs 2a .. 2a+3 (mod N) of its half-index a, and each output n of the
+ * inverse map reads coefficients of half-index (n-2)/2 .. n/2 (mod N/2), so
+ * the outputs that can name i lie within a few places of it; those candidates
+ * are filtered by their own tap lists, and no equation is restated here.
+ * Returns the number of users (at most 8). */
+static int users1d(int inverse, const wavelet_t *w, long N, long i, long o_out[8], double wt_out[8]) {
+    const long half = N / 2;
+    long cand[16];
+    int nc = 0;
+    if (!inverse) {
+        /* forward outputs: approximation a and detail half + a, a near i / 2 */
+        for (long d = -2; d <= 1; ++d) {
+            const long a = ((i / 2 + d) % half + half) % half;
+            cand[nc++] = a;
+            cand[nc++] = half + a;
+        }
+    } else {
+        /* inverse outputs near twice the half-index of coefficient i */
+        const long a = i % half;
+        for (long d = -2; d <= 5; ++d) cand[nc++] = ((2 * a + d) % N + N) % N;
+    }
+    int nu = 0;
+    for (int c = 0; c < nc; ++c) {
+        int dup = 0;
+        for (int k = 0; k < c; ++k) dup |= cand[k] == cand[c];
+        if (dup) continue;
+        long idx[4];
+        double wt[4], acc = 0.0;
+        int hit = 0;
+        const int nt = inverse ? inv1d_taps(w, N, cand[c], idx, wt) : fwd1d_taps(w, N, cand[c], idx, wt);
+        for (int t = 0; t < nt; ++t)
+            if (idx[t] == i) {
+                acc += wt[t];
+                hit = 1;
+            }
+        if (hit) {
+            o_out[nu] = cand[c];
+            wt_out[nu] = acc;
+            ++nu;
+        }
+    }
+    return nu;
+}
+
+/* The output gradient of one band is given on a periodic window of the image:
+ * g[r][s] = gF(y, x) for y = (gy0 + r) mod H, r < hg, and x = (gx0 + s) mod W,
+ * s < wg (gy0 = gx0 = 0, hg = H, wg = W for the whole image).  A read outside
+ * the window gives NaN, which propagates into the evaluated value. */
+typedef struct {
+    const wavelet_t *w;
+    long H, W;
+    double gain;
+    const double *g; /* B planes of hg x wg */
+    long gy0, gx0, hg, wg;
+} adj_ctx;
+
+static double gout_at(const adj_ctx *c, int b, long y, long x) {
+    const long r = ((y - c->gy0) % c->H + c->H) % c->H;
+    const long s = ((x - c->gx0) % c->W + c->W) % c->W;
+    if (r >= c->hg || s >= c->wg) return NAN;
+    return c->g[((long)b * c->hg + r) * c->wg + s];
+}
+
+/* Transpose of the inverse row pass (Eq. 11-16 along a row): value (y, k). */
+static double adj_row_inv(const adj_ctx *c, int b, long y, long k) {
+    long o[8];
+    double wt[8], acc = 0.0;
+    const int nu = users1d(1, c->w, c->W, k, o, wt);
+    for (int t = 0; t < nu; ++t) acc += wt[t] * gout_at(c, b, y, o[t]);
+    return acc;
+}
+
+/* Transpose of the inverse column pass: coefficient (i, k) of Ybar_b. */
+static double adj_col_inv(const adj_ctx *c, int b, long i, long k) {
+    long o[8];
+    double wt[8], acc = 0.0;
+    const int nu = users1d(1, c->w, c->H, i, o, wt);
+    for (int t = 0; t < nu; ++t) acc += wt[t] * adj_row_inv(c, b, o[t], k);
+    return acc;
+}
+
+/* Transpose of the LL swap: the LL quadrant of Ybar_b goes to MS, the rest on. */
+static double adj_swapped(const adj_ctx *c, int b, long i, long k) {
+    if (i < c->H / 2 && k < c->W / 2) return 0.0;
+    return adj_col_inv(c, b, i, k);
+}
+
+/* Transpose of the forward column pass (Eq. 1-6 along a column): value (r, k). */
+static double adj_col_fwd(const adj_ctx *c, int b, long r, long k) {
+    long o[8];
+    double wt[8], acc = 0.0;
+    const int nu = users1d(0, c->w, c->H, r, o, wt);
+    for (int t = 0; t < nu; ++t) acc += wt[t] * adj_swapped(c, b, o[t], k);
+    return acc;
+}
+
+/* Transpose of the forward row pass: this band's share of grad PAN (y, x). */
+static double adj_row_fwd(const adj_ctx *c, int b, long y, long x) {
+    long o[8];
+    double wt[8], acc = 0.0;
+    const int nu = users1d(0, c->w, c->W, x, o, wt);
+    for (int t = 0; t < nu; ++t) acc += wt[t] * adj_col_fwd(c, b, y, o[t]);
+    return acc;
+}
+
+/* The adjoint of the fusion (the map oracle_fuse_adjoint applies to whole
+ * images) evaluated lazily at sampled outputs:
+ *   grad_pan at n pixels (ys[k], xs[k]):  sum_b DWT2^T(Ybar_b, LL zeroed)
+ *   grad_ms of every band at nm MS pixels (is[k], js[k]):  gain * Ybar_b[LL]
+ * with Ybar_b = IDWT2^T(gF_b).  Each transposed pass sums over the users of an
+ * index, taken from the same tap lists as the forward maps.  g: B planes of
+ * the output gradient on the periodic window (gy0, gx0, hg, wg) described at
+ * gout_at; out_ms: B x nm.  A value needing gradient outside the window is NaN. */
+int oracle_fuse_adjoint_points(int kind, long H, long W, int B, double gain, const double *g, long gy0,
+                               long gx0, long hg, long wg, long n, const long *ys, const long *xs,
+                               double *out_pan, long nm, const long *is, const long *js,
+                               double *out_ms) {
+    if (check_shape(kind, H, W) || B < 1) return 1;
+    if (hg < 1 || wg < 1 || hg > H || wg > W) return 1;
+    wavelet_t w = make_wavelet(kind, NULL);
+    adj_ctx c = {&w, H, W, gain, g, gy0, gx0, hg, wg};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < n; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < B; ++b) acc += adj_row_fwd(&c, b, ys[k], xs[k]);
+        out_pan[k] = acc;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < nm; ++k)
+        for (int b = 0; b < B; ++b) out_ms[(long)b * nm + k] = gain * adj_col_inv(&c, b, is[k], js[k]);
+    return 0;
+}
+
 /* ------------------------------------------------------ uint8 output */
 
 /* Reading R6: clamp to [0, 255], then round half to even. */

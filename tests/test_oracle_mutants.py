@@ -50,6 +50,18 @@ MUTANTS = [
      "const int nt = fwd1d_taps(c.w, W, is[k], idx, wt);"),
     ("MS read transposed (point evaluator)", "return c->ms ? c->ms[i * W2 + j] : (double)c->ms_u8[i * W2 + j];",
      "return c->ms ? c->ms[j * W2 + i] : (double)c->ms_u8[i * W2 + j];"),
+    ("point adjoint: LL zeroing bounds", "if (i < c->H / 2 && k < c->W / 2) return 0.0;",
+     "if (i < c->H / 2 && k <= c->W / 2) return 0.0;"),
+    ("point adjoint: forward users miss a neighbour", "for (long d = -2; d <= 1; ++d) {",
+     "for (long d = 0; d <= 1; ++d) {"),
+    ("point adjoint: inverse users miss the next pair", "for (long d = -2; d <= 5; ++d) cand",
+     "for (long d = -2; d <= 1; ++d) cand"),
+    ("point adjoint: grad MS without the gain", "out_ms[(long)b * nm + k] = gain * adj_col_inv(",
+     "out_ms[(long)b * nm + k] = adj_col_inv("),
+    ("point adjoint: window row offset sign", "const long r = ((y - c->gy0) % c->H + c->H) % c->H;",
+     "const long r = ((y + c->gy0) % c->H + c->H) % c->H;"),
+    ("point adjoint: column pass over the row length", "const int nu = users1d(1, c->w, c->H, i, o, wt);",
+     "const int nu = users1d(1, c->w, c->W, i, o, wt);"),
 ]
 
 

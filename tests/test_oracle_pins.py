@@ -207,6 +207,70 @@ def test_dwt2_point_evaluator_matches_whole_image(wav):
 
 # ------------------------------------------------------------------ P8: adjoint
 
+ADJ_SHAPES = [(4, 4), (4, 6), (6, 4), (10, 14), (12, 8), (16, 20)]
+
+
+def _all_points(H, W):
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    ii, jj = np.meshgrid(np.arange(H // 2), np.arange(W // 2), indexing="ij")
+    return yy.ravel(), xx.ravel(), ii.ravel(), jj.ravel()
+
+
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
+@pytest.mark.parametrize("shape", ADJ_SHAPES)
+def test_adjoint_point_evaluator_matches_whole_image(wav, shape):
+    """The lazy point-wise adjoint at every pixel equals the whole-image
+    adjoint (itself pinned to the closed form, the explicit Jacobian and
+    finite differences below).  Haar on integer gradients is exact."""
+    H, W = shape
+    B = 3
+    G = RNG.integers(-50, 51, (B, H, W)).astype(float) if wav == O.HAAR else RNG.standard_normal((B, H, W))
+    gp, gm = O.fuse_adjoint(G, wav)
+    pp, pm = O.fuse_adjoint_points(G, wav, H, W, *_all_points(H, W))
+    if wav == O.HAAR:
+        np.testing.assert_array_equal(pp, gp.ravel())
+        np.testing.assert_array_equal(pm, gm.reshape(B, -1))
+    else:
+        assert np.abs(pp - gp.ravel()).max() < 1e-13
+        assert np.abs(pm - gm.reshape(B, -1)).max() < 1e-13
+
+
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
+def test_adjoint_point_evaluator_matches_closed_form(wav):
+    """P8 closed form: grad_MS_b = gain sigma^2 L_H G_b L_W^T and
+    grad_PAN = sum_b (G_b - sigma^2 L_H^T L_H G_b L_W^T L_W), at every pixel."""
+    H, W, B = 12, 10, 2
+    G = RNG.standard_normal((B, H, W))
+    gain = O.default_gain(wav)
+    pp, pm = O.fuse_adjoint_points(G, wav, H, W, *_all_points(H, W))
+    cgp = sum(M.adjoint_closed_form(G[b], wav, gain)[0] for b in range(B))
+    cgm = np.stack([M.adjoint_closed_form(G[b], wav, gain)[1] for b in range(B)])
+    assert np.abs(pp - cgp.ravel()).max() < 1e-12
+    assert np.abs(pm - cgm.reshape(B, -1)).max() < 1e-12
+
+
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
+def test_adjoint_point_evaluator_on_a_periodic_window(wav):
+    """Given only a window of the output gradient that wraps past the image's
+    last row and column, the points inside it (with a 4-pixel margin) equal the
+    whole-image adjoint; a point whose taps leave the window is refused."""
+    H, W, B = 16, 20, 2
+    G = RNG.standard_normal((B, H, W))
+    gp, gm = O.fuse_adjoint(G, wav)
+    gy0, gx0, hg, wg = H - 5, W - 6, 12, 14          # rows 11..15, 0..6; columns 14..19, 0..7
+    rows = (gy0 + np.arange(hg)) % H
+    cols = (gx0 + np.arange(wg)) % W
+    win = G[:, rows][:, :, cols]
+    ys = np.array([14, 15, 0, 1, 2, 15, 0])
+    xs = np.array([18, 19, 0, 1, 2, 0, 19])
+    iis, jjs = np.array([7, 0, 0, 7]), np.array([9, 0, 9, 0])
+    pp, pm = O.fuse_adjoint_points(win, wav, H, W, ys, xs, iis, jjs, gy0=gy0, gx0=gx0)
+    assert np.abs(pp - gp[ys, xs]).max() < 1e-13
+    assert np.abs(pm - gm[:, iis, jjs]).max() < 1e-13
+    with pytest.raises(ValueError):
+        O.fuse_adjoint_points(win, wav, H, W, [8], [4], gy0=gy0, gx0=gx0)
+
+
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
 def test_adjoint_closed_form_and_dot_product(wav):
     H, W, B = 12, 16, 3
