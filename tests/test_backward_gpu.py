@@ -134,6 +134,39 @@ def test_autograd_unbatched_shapes():
     assert pan.grad.shape == pan.shape and ms.grad.shape == ms.shape
 
 
+def test_autograd_config3_elementwise():
+    """The autograd workload as timed: a batch of 8 scenes, PAN 4096^2 and 4 MS
+    bands 2048^2 generated as 8-bit scenes and cast to float32, D4, through
+    DWTFuseFn (batched forward and batched adjoint).  With a seeded output
+    gradient, grad_PAN and every band's grad_MS equal the oracle's point-wise
+    adjoint element by element on two seeded 256 x 256 windows per scene and on
+    every scene's wrap rows and columns; the fused bands match the point-wise
+    oracle on the same windows."""
+    from tests.parity_windows import adjoint_region_error, forward_region_error, regions
+    N, B, H, W = 8, 4, 4096, 4096
+    pans, mss = [], []
+    for i in range(N):
+        p, m = scenegen.make_scene(H, W, B, seed=i, device=DEV)
+        pans.append(p.float())
+        mss.append(m.float())
+    pan = torch.stack(pans).requires_grad_(True)
+    ms = torch.stack(mss).requires_grad_(True)
+    del pans, mss
+    G = scenegen.target_like((N, B, H, W), seed=77, device=DEV)
+    out = DWTFuseFn.apply(pan, ms, O.D4)
+    out.backward(G)
+    torch.cuda.synchronize()
+    for i in range(N):
+        pan_h = pan[i].detach().cpu().numpy().astype(np.float64)
+        ms_h = ms[i].detach().cpu().numpy().astype(np.float64)
+        for k, reg in enumerate(regions(H, W, seed=100 + i)):
+            e = adjoint_region_error(G[i], pan.grad[i], ms.grad[i], O.D4, reg)
+            assert e <= 1e-4, (i, reg, e)
+            if k < 2:
+                ef = forward_region_error(pan_h, ms_h, out[i].detach(), O.D4, reg, range(B))
+                assert ef <= 5e-4, (i, reg, ef)
+
+
 def test_dot_product_identity_config3_size():
     """<F(x), y> = <x, F^T(y)> at the autograd workload's scene size
     (PAN 4096^2, 4 MS bands 2048^2, float32), dot products in FP64."""

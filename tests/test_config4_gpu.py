@@ -1,12 +1,15 @@
 """Full-size batched forward + backward with metrics: scenes of the 12-scene
-workload (square PAN, sides even in [8192, 32768], 8 MS bands, D4), streamed
-through one output slot: batched forward (float32 + uint8), ERGAS/QNR of the
-uint8 product, and the adjoint with grad_out = F (loss 1/2 ||F||^2).
+workload (square PAN, sides even in [8192, 32768], 8 MS bands, D4), one at a
+time: batched forward (float32 + uint8), ERGAS/QNR of the uint8 product, and
+the adjoint of a seeded output gradient G.
 
-Checked per scene: sampled fused pixels against the point-wise oracle (D4 bar
-5e-4), the dot-product identity <F(P, M), F> = <P, grad_P> + <M, grad_M> in
-FP64 (holds at any size), and, on the smallest scene, the metrics against the
-oracle on the whole images (uint8 bars of test_metrics_gpu)."""
+Checked per scene, element by element against the oracle's point-wise
+evaluators: the fused bands on two seeded 256 x 256 windows and on the wrap
+rows and columns (D4 bar 5e-4), grad_PAN and every band's grad_MS on the same
+regions (bar 1e-4 of max(1, max |ref|)); as extra checks the dot-product
+identity <F(P, M), G> = <P, grad_P> + <M, grad_M> in FP64, and, on the
+smallest scene, the metrics against the oracle on the whole images (uint8
+bars of test_metrics_gpu)."""
 import numpy as np
 import pytest
 import torch
@@ -45,15 +48,17 @@ def _run_scene(sp, ws, mws):
     _C.dwtfuse_fuse_batched([_C.make_scene(pan, ms, sp.wavelet, out, out8)], ws)
     res = torch.zeros(4, dtype=torch.float64, device=DEV)
     _C.dwtfuse_metrics(out8, ms, pan, mws, res)
+    G = scenegen.target_like((8, H, W), seed=sp.seed + 5, device=DEV)
     gp = torch.empty((H, W), device=DEV)
     gm = torch.empty((8, H // 2, W // 2), device=DEV)
-    _C.dwtfuse_fuse_backward(out, sp.wavelet, gp, gm)  # grad of 1/2 ||F||^2 is F
+    _C.dwtfuse_fuse_backward(G, sp.wavelet, gp, gm)
     torch.cuda.synchronize()
-    return pan, ms, out, out8, res.cpu().numpy(), gp, gm
+    return pan, ms, out, out8, res.cpu().numpy(), G, gp, gm
 
 
 @pytest.mark.parametrize("which", ["smallest", "largest"])
 def test_config4_scene(which):
+    from tests.parity_windows import adjoint_region_error, forward_region_error, regions
     specs = config4_specs()
     if which == "largest":
         sp = max(specs, key=lambda s: s.H)
@@ -62,25 +67,22 @@ def test_config4_scene(which):
         sp = min(specs, key=lambda s: s.H)
     ws = torch.zeros(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=DEV)
     mws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=DEV)
-    pan, ms, out, out8, res, gp, gm = _run_scene(sp, ws, mws)
+    pan, ms, out, out8, res, G, gp, gm = _run_scene(sp, ws, mws)
     H = W = sp.H
     assert _C.dwtfuse_get_last_device_status(ws) == _C.OK
-    rng = np.random.default_rng(sp.seed)
-    ys = np.concatenate([[0, 1, H - 2, H - 1], rng.integers(0, H, 300)])
-    xs = np.concatenate([[0, W - 1, 1, W - 2], rng.integers(0, W, 300)])
-    yt, xt = torch.from_numpy(ys).to(DEV), torch.from_numpy(xs).to(DEV)
-    pan_h = pan.cpu().numpy()
-    for b in (0, 7):
-        ref = O.fuse_points(pan_h, ms[b].cpu().numpy(), sp.wavelet, ys, xs)
-        got = out[b][yt, xt].cpu().numpy().astype(np.float64)
-        assert np.abs(got - ref).max() <= 5e-4
-    lhs = dot64(out, out)
+    pan_h, ms_h = pan.cpu().numpy(), ms.cpu().numpy()
+    for reg in regions(H, W, seed=sp.seed):
+        ef = forward_region_error(pan_h, ms_h, out, sp.wavelet, reg, range(8))
+        assert ef <= 5e-4, (reg, ef)
+        eb = adjoint_region_error(G, gp, gm, sp.wavelet, reg)
+        assert eb <= 1e-4, (reg, eb)
+    lhs = dot64(out, G)
     rhs = dot64(pan, gp) + dot64(ms, gm)
-    assert abs(lhs - rhs) <= 1e-5 * lhs
+    assert abs(lhs - rhs) <= 1e-6 * (dot64(out, out) * dot64(G, G)) ** 0.5
     assert np.isfinite(res).all()
     if which == "smallest":
         f = out8.cpu().numpy()
-        m = list(ms.cpu().numpy())
+        m = list(ms_h)
         q, dl, ds = O.qnr(f, m, pan_h)
         ref = np.array([O.ergas(f, m), q, dl, ds])
         assert abs(res[0] - ref[0]) <= 1e-12 * ref[0]

@@ -177,8 +177,11 @@ def test_two_call_form_rejects_unsupported(ws):
 def test_benchmark_step_full_size(ws):
     """The benchmark step as timed (D4, PAN 16384^2 uint8, 6 MS bands 8192^2,
     float32 + uint8 outputs, one dwtfuse_fuse_metrics call): outputs equal the
-    plain forward's bits, the metrics equal the oracle's on the whole images,
-    and sampled float32 pixels equal the oracle's point-wise closed form."""
+    plain forward's bits; every pixel of every float32 band is within 5e-4 of
+    the whole-image oracle, every uint8 pixel follows the rounding rule on the
+    oracle's value (off by one only within 5e-4 of a tie); the metrics equal
+    the oracle's on the whole images."""
+    from tests.test_fuse_gpu import check_u8
     H = W = 16384
     pan, ms = scenegen.make_scene(H, W, 6, seed=0, blob_scale=16.0, device=DEV)
     of, ou, r = fused_path(pan, ms, O.D4, ws)
@@ -188,13 +191,17 @@ def test_benchmark_step_full_size(ws):
     torch.cuda.synchronize()
     assert torch.equal(of, f2) and torch.equal(ou, u2)
     del f2, u2
-    rng = np.random.default_rng(5)
     p, m = pan.cpu().numpy(), ms.cpu().numpy()
-    ii, jj = rng.integers(0, H, 64), rng.integers(0, W, 64)
+    pf = p.astype(np.float64)
     for b in range(6):
-        ref = O.fuse_points(p, m[b], O.D4, ii, jj)
-        got = of[b].cpu().numpy()[ii, jj]
-        assert np.abs(got - ref).max() <= 5e-4
+        ref = O.fuse(pf, [m[b]], O.D4)[0]
+        got = of[b].cpu().numpy()
+        err = float(np.abs(got - ref).max())
+        assert err <= 5e-4, (b, err)
+        del got
+        check_u8(ou[b].cpu().numpy(), ref, O.D4)
+        del ref
+    del pf
     f = ou.cpu().numpy()
     q, dl, ds = O.qnr(f, list(m), p)
     ref = np.array([O.ergas(f, list(m)), q, dl, ds])
