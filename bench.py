@@ -64,8 +64,9 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, vendor figure (context; the measured co
 # forward-and-score kernel at this workload, keyed by the hash of the kernel
 # sources it was taken on.
 KNOWN_TRAFFIC: dict[str, float] = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), full size:
-    # read 689,832,448 + write 7,991,618,304 (profiles/fuse_metrics_d4_4096x4096_b6.md)
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the
+    # default workload at full size, captured with the step's launch list:
+    # read 689,832,448 + write 7,991,618,304
     "88490acee432": 8681450752.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")

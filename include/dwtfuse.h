@@ -296,10 +296,12 @@ int dwtfuse_get_last_device_status(const void *workspace, void *stream);
  * until the process exits.
  *
  * Arguments and results are those of dwtfuse_fuse_batched without the
- * workspace.  More than DWTFUSE_MAX_SCENES scenes is DWTFUSE_ESHAPE; a launch
- * whose queue needs more scratch than the array holds is DWTFUSE_ENOMEM.
+ * workspace.  More than DWTFUSE_MAX_SCENES scenes is DWTFUSE_ESHAPE (the
+ * queue's 16 bytes fit the array for every legal call).
  * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture.  cudaDeviceReset on a device makes
+ * the kept address stale: do not call this entry point on that device again.
  * Every call shares the one array, which keeps the last call's contents; each
  * call clears the counter and status word on its stream before its kernel.
  * Calls that overlap on the GPU (unordered streams) race on the counter, so

@@ -56,7 +56,6 @@ extern "C" int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, 
                                             int blocks_per_sm, void *stream) {
     if (!scenes || n < 1 || rows_per_item < 0 || blocks_per_sm < 0) return DWTFUSE_EINVAL;
     if (n > kMaxScenes) return DWTFUSE_ESHAPE;
-    if (kQueueBytes > DWTFUSE_STATIC_SCRATCH_BYTES) return DWTFUSE_ENOMEM;
     static thread_local BatchTable t;
     int st = build_batch_table(scenes, n, rows_per_item, &t);
     if (st != DWTFUSE_OK) return st;
