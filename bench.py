@@ -13,7 +13,9 @@ and the reduction.
   value     fused Gpx/s = PAN pixels x bands per second, inputs resident in HBM
   e2e       the same metric with the inputs copied host -> device from pinned
             memory and the uint8 fused bands and quality figures copied back
-            every step (copies and compute of neighbouring steps overlap)
+            every step (copies and compute of neighbouring steps overlap); the
+            float32 bands stay on the device, so seen from the host this is a
+            uint8-out pipeline
   roofline  the forward-and-score kernel (the step's dominant kernel, ~89 % of
             it): algorithmic bytes per launch (inputs read once, both outputs
             written once) / mean launch time, from CUDA events on the launch
@@ -68,6 +70,9 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # default workload at full size, captured with the step's launch list:
     # read 689,832,448 + write 7,991,618,304
     "88490acee432": 8681450752.0,
+    # the same capture after the row-band fields joined the tile header:
+    # read 689,828,693 + write 7,989,620,992 (mean of 3 launches)
+    "3c44d97b0575": 8679449685.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
@@ -337,7 +342,10 @@ def measure_e2e(args, pan, ms, out_f, mws, stream, world, dev) -> dict:
             "h2d_bytes_per_step": pan.numel() + ms.numel(),
             "d2h_bytes_per_step": out_u[0].numel() + 4 * 8,
             "steps": Ke, "runs": [round(t, 2) for t in trials], "statistic": "median of 3 runs",
-            "pipelined": "3 streams, 2 buffer sets"}
+            "pipelined": "3 streams, 2 buffer sets",
+            "returned": "the uint8 fused bands and the four quality figures; the float32 fused "
+                        "bands the step also writes stay in device memory (a uint8-out pipeline "
+                        "seen from the host)"}
 
 
 def _time_ms(fn, reps: int, stream) -> float:
@@ -743,6 +751,26 @@ def run_case(args) -> None:
         ou = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
         call = lambda: _C.dwtfuse_fuse(pan, ms, WAVELET, of, ou)  # noqa: E731
         nbytes = H * W * (1.0 + B * (0.25 + 4.0 + 1.0))
+    elif args.case in ("dwt2", "idwt2"):
+        Z = torch.empty((H, W), dtype=torch.float32, device=dev)
+        _C.dwtfuse_dwt2(pan, WAVELET, Z)
+        if args.case == "dwt2":
+            call = lambda: _C.dwtfuse_dwt2(pan, WAVELET, Z)  # noqa: E731
+            nbytes = H * W * 5.0  # uint8 image in, float coefficients out
+        else:
+            img = torch.empty((H, W), dtype=torch.float32, device=dev)
+            call = lambda: _C.dwtfuse_idwt2(Z, WAVELET, img)  # noqa: E731
+            nbytes = H * W * 8.0  # float coefficients in, float image out
+    elif args.case == "rows":
+        from paper_1803_00737_gb300 import shard
+        parts = shard.row_bands(H, 4)
+        slabs = [(y0, y1, *shard.make_slab(pan, ms, y0, y1, WAVELET)) for y0, y1 in parts]
+        outs = [torch.empty((B, y1 - y0, W), dtype=torch.float32, device=dev) for y0, y1 in parts]
+
+        def call():  # the scene as 4 row bands, each from its slab
+            for (y0, y1, ps, mss), o in zip(slabs, outs):
+                _C.dwtfuse_fuse_rows(ps, mss, WAVELET, H, y0, y1, o, None)
+        nbytes = H * W * (1.0 + B * (0.25 + 4.0))
     else:  # backward
         g = scenegen.target_like((B, H, W), seed=1000, device=dev)
         gp = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -781,7 +809,7 @@ def main() -> None:
                     help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--case", choices=["metrics", "fuse", "backward"],
+    ap.add_argument("--case", choices=["metrics", "fuse", "backward", "dwt2", "idwt2", "rows"],
                     help="time one library call alone at --side x --width with --bands (profiling aid)")
     ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
     ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")

@@ -96,6 +96,29 @@ int dwtfuse_fuse_ex(const void *pan, const void *const *ms, int bands, int64_t H
                     void *stream);
 
 /*
+ * Fused forward of one band of PAN rows [y0, y1) of an H x W scene, from a
+ * slab that carries the band's halo rows (Sec. 3 splits the source image
+ * into parts for the nodes of a cluster; with the periodic wrap of Eq. 5-6
+ * and 13-14 a D4 part needs its neighbours' rows, which the paper's merge of
+ * separately fused parts leaves out).  The result equals rows [y0, y1) of
+ * dwtfuse_fuse on the whole scene bit for bit, for any split.  With
+ * h = 2 PAN rows and hm = 1 MS row for D4 (0 and 0 for Haar):
+ *   pan_slab  PAN rows y0 - h .. y1 + h - 1, each taken mod H (the first and
+ *             last parts carry the rows of the image's other end), W columns
+ *   ms_slab   host array of `bands` device pointers, each holding MS rows
+ *             y0/2 - hm .. y1/2 - 1 (mod H/2), W/2 columns
+ *   out_f32   [bands][y1 - y0][W] float, or NULL
+ *   out_u8    [bands][y1 - y0][W] uint8, or NULL
+ * y0, y1 even, 0 <= y0 < y1 <= H, else DWTFUSE_ESHAPE; H, W, bands, dtypes,
+ * alignment and errors as for dwtfuse_fuse.  Serves a scene split across
+ * devices (each fuses its own rows after receiving its halo rows) and scenes
+ * processed in row bands to bound device memory.
+ */
+int dwtfuse_fuse_rows(const void *pan_slab, const void *const *ms_slab, int bands, int64_t H, int64_t W,
+                      int64_t y0, int64_t y1, int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8,
+                      void *stream);
+
+/*
  * One-level 2D DWT of an image (Sec. 2: 1D transform of every row, then of
  * every column; Haar Eq. 1-2, Daubechies-4 Eq. 3-10 with periodic wrap), the
  * transform the fusion applies before the LL replacement.

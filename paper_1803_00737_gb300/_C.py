@@ -72,6 +72,8 @@ _SIGS = {
     "dwtfuse_fuse": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, _vp, _vp, _vp]),
     "dwtfuse_fuse_ex": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i, _i, ctypes.c_float, _vp, _vp,
                              _vp]),
+    "dwtfuse_fuse_rows": (_i, [_vp, ctypes.POINTER(_vp), _i, _i64, _i64, _i64, _i64, _i, _i, _vp, _vp,
+                               _vp]),
     "dwtfuse_dwt2": (_i, [_vp, _i, _i64, _i64, _i, _vp, _vp]),
     "dwtfuse_idwt2": (_i, [_vp, _i64, _i64, _i, _vp, _vp, _vp]),
     "dwtfuse_fuse_backward": (_i, [_vp, _i, _i64, _i64, _i, _vp, ctypes.POINTER(_vp), _vp]),
@@ -206,6 +208,40 @@ def dwtfuse_fuse_ex(pan: torch.Tensor, ms, wavelet: int, ll_gain: float,
                                _dev(out_u8, "out_u8") if out_u8 is not None else None,
                                _stream(stream))
     _check(st, "dwtfuse_fuse_ex")
+
+
+def row_halo(wavelet: int) -> tuple[int, int]:
+    """(PAN rows, MS rows) of halo above a row band's slab (the PAN halo is
+    also taken below): 2 and 1 for D4, none for Haar."""
+    return (2, 1) if int(wavelet) == D4 else (0, 0)
+
+
+def dwtfuse_fuse_rows(pan_slab: torch.Tensor, ms_slab, wavelet: int, H: int, y0: int, y1: int,
+                      out_f32: torch.Tensor | None = None, out_u8: torch.Tensor | None = None,
+                      stream=None) -> None:
+    """Fused rows [y0, y1) of an H x W scene from a slab with halo rows (see
+    dwtfuse_fuse_rows in dwtfuse.h): pan_slab (y1 - y0 + 2h, W), ms_slab
+    (B, (y1 - y0)/2 + hm, W/2), outputs (B, y1 - y0, W)."""
+    bands = _bands(ms_slab)
+    h, hm = row_halo(wavelet)
+    n_rows = y1 - y0
+    Hs, W = pan_slab.shape
+    if Hs != n_rows + 2 * h:
+        raise ValueError(f"pan_slab must hold {n_rows + 2 * h} rows (band plus halo), got {Hs}")
+    code = _dtype_code(pan_slab, "pan_slab")
+    for b, m in enumerate(bands):
+        if m.dtype != pan_slab.dtype or tuple(m.shape) != (n_rows // 2 + hm, W // 2):
+            raise ValueError(f"ms_slab[{b}] must be {pan_slab.dtype} of shape ({n_rows // 2 + hm}, {W // 2})")
+    for name, o, dt in (("out_f32", out_f32, torch.float32), ("out_u8", out_u8, torch.uint8)):
+        if o is not None and (o.dtype != dt or tuple(o.shape) != (len(bands), n_rows, W)):
+            raise ValueError(f"{name} must be {dt} of shape ({len(bands)}, {n_rows}, {W})")
+    ptrs = (_vp * len(bands))(*[_dev(m, f"ms_slab[{b}]") for b, m in enumerate(bands)])
+    st = lib().dwtfuse_fuse_rows(_dev(pan_slab, "pan_slab"), ptrs, len(bands), int(H), W, int(y0), int(y1),
+                                 int(wavelet), code,
+                                 _dev(out_f32, "out_f32") if out_f32 is not None else None,
+                                 _dev(out_u8, "out_u8") if out_u8 is not None else None,
+                                 _stream(stream))
+    _check(st, "dwtfuse_fuse_rows")
 
 
 def dwtfuse_dwt2(img: torch.Tensor, wavelet: int, coeffs: torch.Tensor, stream=None) -> None:

@@ -140,6 +140,9 @@ int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int
                         (!out_u8 || aligned(out_u8, 4));
     s->a4 = (W % 4 == 0) && vec_ok;
     s->alt = (W % 4 == 2) && vec_ok;
+    s->out_plane = H * W;
+    s->m_lo = 0;
+    s->m_hi = (int32_t)(H / 2);
     return DWTFUSE_OK;
 }
 
@@ -240,6 +243,27 @@ int dwtfuse_fuse_ex(const void *pan, const void *const *ms, int bands, int64_t H
     const int st = make_scene(pan, ms, bands, H, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
     if (st != DWTFUSE_OK) return st;
     s.gain = ll_gain;
+    return cuda_status(launch_fuse(s, rows_per_item(), 0, static_cast<cudaStream_t>(stream)));
+}
+
+int dwtfuse_fuse_rows(const void *pan_slab, const void *const *ms_slab, int bands, int64_t H, int64_t W,
+                      int64_t y0, int64_t y1, int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8,
+                      void *stream) {
+    int st = check_shape(H, W, wavelet);
+    if (st != DWTFUSE_OK) return st;
+    if ((y0 & 1) || (y1 & 1) || y0 < 0 || y1 > H || y1 <= y0) return DWTFUSE_ESHAPE;
+    // The slab is a scene of its own whose MS rows [m_lo, m_hi) are the band's:
+    // D4 reads PAN rows 2m-2 .. 2m+3 and MS rows m-1, m for MS row m, so with
+    // 2 PAN rows and 1 MS row of halo above and 2 PAN rows below, no read of
+    // the band wraps inside the slab; the whole image's wrap is in the halo.
+    const int64_t halo = wavelet == DWTFUSE_D4 ? 2 : 0;
+    const int64_t Hs = (y1 - y0) + 2 * halo;
+    SceneArgs s;
+    st = make_scene(pan_slab, ms_slab, bands, Hs, W, wavelet, in_dtype, out_f32, out_u8, kMaxBands, &s);
+    if (st != DWTFUSE_OK) return st;
+    s.out_plane = (y1 - y0) * W;
+    s.m_lo = (int32_t)(halo / 2);
+    s.m_hi = (int32_t)(halo / 2 + (y1 - y0) / 2);
     return cuda_status(launch_fuse(s, rows_per_item(), 0, static_cast<cudaStream_t>(stream)));
 }
 

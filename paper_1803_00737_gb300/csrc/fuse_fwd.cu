@@ -131,8 +131,10 @@ cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream
         e = sm_count(&sms);
         if (e != cudaSuccess) return e;
         const int64_t cap = (int64_t)sms * occ;
-        int Rl = R > 0 ? R : balanced_rows(s.H, s.W, cap * kWarps);
-        const ItemGrid g = item_grid(s.H, s.W, Rl);
+        // Items cover the MS rows [m_lo, m_hi) (all of them for a whole scene).
+        const int64_t rows2 = 2 * (int64_t)(s.m_hi - s.m_lo);
+        int Rl = R > 0 ? R : balanced_rows(rows2, s.W, cap * kWarps);
+        const ItemGrid g = item_grid(rows2, s.W, Rl);
         const int64_t need = (g.items + kWarps - 1) / kWarps;
         const unsigned grid = (unsigned)(need < cap ? need : cap);
         if (grid == 0) continue;

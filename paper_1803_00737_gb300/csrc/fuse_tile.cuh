@@ -157,7 +157,7 @@ __device__ __forceinline__ void store4_shifted(const OutPtrs &o, int64_t off, in
 // ------------------------------------------------------------------ scene
 
 // Everything a warp needs about one scene.  Band pointers are typed by the
-// kernel template (TIn); the plane stride of the outputs is H*W.
+// kernel template (TIn); the plane stride of the outputs is out_plane.
 struct SceneArgs {
     const void *pan;
     const void *ms[kMaxBands];
@@ -170,6 +170,9 @@ struct SceneArgs {
     float gain;
     int32_t a4;        // W % 4 == 0 and PAN/outputs aligned for 4-pixel vectors
     int32_t alt;       // W % 4 == 2 with aligned planes: even rows aligned, odd rows 2 px past
+    int64_t out_plane; // elements between output band planes (H * W for a whole scene)
+    int32_t m_lo;      // MS rows [m_lo, m_hi) are fused; output row 0 belongs to MS row m_lo
+    int32_t m_hi;      // (0 and H/2 for a whole scene; a row band's slab starts past its halo)
 };
 
 // Column bookkeeping of one lane for one strip (sides are < 2^20, so 32 bits).
@@ -401,20 +404,20 @@ struct DirectEmit {
     bool a4, a4e, alt;
 
     __device__ __forceinline__ void band(int b, int64_t m, const float *v0, const float *v1, float, float) const {
-        const int64_t W = s.W, HW = s.H * s.W;
+        const int64_t W = s.W, HW = s.out_plane, y = 2 * (m - s.m_lo);
         if constexpr (ALT) {
             OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
                       s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
-            if (c.active) store4(o, (2 * m) * W + c.x, a4e, c.two, v0);
+            if (c.active) store4(o, y * W + c.x, a4e, c.two, v0);
             if (alt)
-                store4_shifted(o, (2 * m + 1) * W + c.x, lane, c.active, c.two, c.last, v1);
+                store4_shifted(o, (y + 1) * W + c.x, lane, c.active, c.two, c.last, v1);
             else if (c.active)
-                store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+                store4(o, (y + 1) * W + c.x, a4, c.two, v1);
         } else if (c.active) {
             OutPtrs o{s.out_f32 ? s.out_f32 + (int64_t)(b0 + b) * HW : nullptr,
                       s.out_u8 ? s.out_u8 + (int64_t)(b0 + b) * HW : nullptr};
-            store4(o, (2 * m) * W + c.x, a4, c.two, v0);
-            store4(o, (2 * m + 1) * W + c.x, a4, c.two, v1);
+            store4(o, y * W + c.x, a4, c.two, v0);
+            store4(o, (y + 1) * W + c.x, a4, c.two, v1);
         }
     }
     __device__ __forceinline__ void row_end(int64_t, const float *, const float *) const {}
@@ -460,8 +463,8 @@ __device__ __forceinline__ void run_item(const SceneArgs &s, int64_t item, int64
                                          int b0, int nb, int lane) {
     const int64_t sx = item % strips_x, sy = item / strips_x;
     const int64_t x0 = sx * kWarpCols;
-    const int64_t m_s = sy * R;
-    const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
+    const int64_t m_s = s.m_lo + sy * R;
+    const int64_t m_e = min(m_s + (int64_t)R, (int64_t)s.m_hi);
     if (WAV == 0 || (WAV < 0 && s.wavelet == 0))
         direct_item<T, 0, NB, ALT>(s, x0, m_s, m_e, b0, nb, lane);
     else
