@@ -73,6 +73,9 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # the same capture after the row-band fields joined the tile header:
     # read 689,828,693 + write 7,989,620,992 (mean of 3 launches)
     "3c44d97b0575": 8679449685.0,
+    # after the scoring emitter took 7-8 bands (the 6-band body unchanged):
+    # read 689,794,219 + write 7,989,526,784 (mean of 3 launches)
+    "af32194f41e5": 8679321003.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
 
@@ -493,24 +496,25 @@ def measure_config4(args, dev, peak: float) -> dict:
         views.append((sp, p, m, f, u, gp_s[:n].view(sp.H, sp.W),
                       gm_s[:B * n // 4].view(B, sp.H // 2, sp.W // 2), _C.make_scene(p, m, sp.wavelet, f, u)))
 
-    def run(ev=None):
+    def run():  # per scene: forward scoring its uint8 product on chip, MS pass, finalize; adjoint
         for k, (sp, p, m, f, u, gp, gm, scene) in enumerate(views):
-            if ev is not None:
-                ev[k][0].record()
-            _C.dwtfuse_fuse_batched([scene], ws)
-            if ev is not None:
-                ev[k][1].record()
-            _C.dwtfuse_metrics(u, m, p, mws, res[k])
-            if ev is not None:
-                ev[k][2].record()
+            _C.dwtfuse_fuse_metrics(p, m, sp.wavelet, f, u, mws, res[k])
             _C.dwtfuse_fuse_backward(f, sp.wavelet, gp, gm)
-            if ev is not None:
-                ev[k][3].record()
+
+    def run_phases(ev):  # the same work with the two halves of the metrics call apart, for timing
+        for k, (sp, p, m, f, u, gp, gm, scene) in enumerate(views):
+            ev[k][0].record()
+            _C.dwtfuse_fuse_and_score(p, m, sp.wavelet, f, u, mws)
+            ev[k][1].record()
+            _C.dwtfuse_score_finish(m, p, u, mws, res[k])
+            ev[k][2].record()
+            _C.dwtfuse_fuse_backward(f, sp.wavelet, gp, gm)
+            ev[k][3].record()
 
     run()
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in views]
-    run(ev)
+    run_phases(ev)
     torch.cuda.synchronize()
     t_f = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
     t_m = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
@@ -529,25 +533,29 @@ def measure_config4(args, dev, peak: float) -> dict:
     ms_graph = _time_ms(g.replay, max(1, min(3, args.form_reps)), torch.cuda.current_stream())
     px = sum(sp.H * sp.W for sp in specs)
     units = px * B
-    fb = px * (1.0 + B * (0.25 + 4.0 + 1.0))
-    mb = px * (B * 1.0 + 1.0 + B * 0.25) + px * (B * 0.25 + 1.0)
+    fb = px * (1.0 + B * (0.25 + 4.0 + 1.0))  # the forward's bytes; its scoring reads nothing more
+    mb = px * (B * 0.25 + 1.0)  # MS-resolution pass: MS and PAN read once
     bb = px * (4.0 * B + 4.0 + B)
     rf = lambda nbytes, t: {"achieved": nbytes / t / 1e9, "frac": nbytes / t / 1e9 / peak}  # noqa: E731
     q = res.cpu().numpy()
     del views, inputs, out_f, out_u, gp_s, gm_s, g
     torch.cuda.empty_cache()
     return {
-        "workload": "12 square scenes, PAN sides even U[8192, 32768] uint8, 8 MS bands, D4: batched "
-                    "forward (float32 + uint8) + ERGAS/QNR of the uint8 product + adjoint with "
-                    "grad_out = F, one CUDA graph, outputs streamed through one slot"
+        "workload": "12 square scenes, PAN sides even U[8192, 32768] uint8, 8 MS bands, D4: forward "
+                    "(float32 + uint8) scoring its uint8 product on chip + MS-resolution pass and "
+                    "finalize of ERGAS/QNR + adjoint with grad_out = F, one CUDA graph, outputs "
+                    "streamed through one slot"
                     + (" [reduced: --forms-small]" if args.forms_small else ""),
         "scenes": [sp.H for sp in specs], "pan_gpx": px / 1e9,
         "fwd_bwd_metrics_gpxs": units / (ms_graph / 1e3) / 1e9, "unit": UNIT, "graph_ms": ms_graph,
-        "per_kernel": {"fused_forward": {"ms": t_f * 1e3, **rf(fb, t_f)},
-                       "metrics": {"ms": t_m * 1e3, **rf(mb, t_m)},
+        "per_kernel": {"fused_forward": {"ms": t_f * 1e3, **rf(fb, t_f),
+                                         "note": "forward + PAN-resolution scoring on chip"},
+                       "metrics": {"ms": t_m * 1e3, **rf(mb, t_m),
+                                   "note": "MS-resolution pass + finalize (the PAN-resolution sums "
+                                           "come from the forward, no read-back of the product)"},
                        "adjoint": {"ms": t_b * 1e3, **rf(bb, t_b)}},
         "qnr_range": [float(q[:, 1].min()), float(q[:, 1].max())],
-        "gpu_launches_per_replay": len(specs) * (1 + 3 + 2),
+        "gpu_launches_per_replay": len(specs) * (3 + 2),
     }
 
 
@@ -751,6 +759,12 @@ def run_case(args) -> None:
         ou = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
         call = lambda: _C.dwtfuse_fuse(pan, ms, WAVELET, of, ou)  # noqa: E731
         nbytes = H * W * (1.0 + B * (0.25 + 4.0 + 1.0))
+    elif args.case == "fuse_score":  # the forward that scores its uint8 product on chip
+        of = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+        ou = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+        ws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
+        call = lambda: _C.dwtfuse_fuse_and_score(pan, ms, WAVELET, of, ou, ws)  # noqa: E731
+        nbytes = H * W * (1.0 + B * (0.25 + 4.0 + 1.0))
     elif args.case in ("dwt2", "idwt2"):
         Z = torch.empty((H, W), dtype=torch.float32, device=dev)
         _C.dwtfuse_dwt2(pan, WAVELET, Z)
@@ -809,7 +823,7 @@ def main() -> None:
                     help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--case", choices=["metrics", "fuse", "backward", "dwt2", "idwt2", "rows"],
+    ap.add_argument("--case", choices=["metrics", "fuse", "fuse_score", "backward", "dwt2", "idwt2", "rows"],
                     help="time one library call alone at --side x --width with --bands (profiling aid)")
     ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
     ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")

@@ -208,7 +208,7 @@ int dwtfuse_qnr(const void *fused, int fused_dtype, const void *const *ms, const
  * the same outputs as dwtfuse_fuse(pan, ms, ..., out_f32, out_u8) and then
  * dwtfuse_metrics(out_u8, DWTFUSE_U8, ms, pan, in_dtype, ...) into
  * out_device (ERGAS, QNR, D_lambda, D_s as four device doubles).  With uint8
- * inputs and up to 6 bands the forward scores its product on chip (the
+ * inputs (up to 8 bands, as the metrics) the forward scores its product on chip (the
  * PAN-resolution half of the metrics needs no read of the fused bands, PAN or
  * MS); otherwise the two calls run one after the other.  Arguments and errors
  * are those of the two calls; out_u8 is required, out_f32 optional; the
@@ -223,7 +223,7 @@ int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int6
 /*
  * dwtfuse_fuse_metrics in two calls on the same workspace, for callers that
  * schedule or time the halves apart.  dwtfuse_fuse_and_score launches only
- * the fused forward that scores its product (uint8 inputs, <= 6 bands; else
+ * the fused forward that scores its product (uint8 inputs, <= 8 bands; else
  * DWTFUSE_ESHAPE) and leaves the partial scores in the workspace;
  * dwtfuse_score_finish then runs the MS-resolution pass and the reduction
  * into out_device.  The second call must follow the first on the same
@@ -341,6 +341,20 @@ int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, int rows_pe
  * Process-wide.
  */
 int dwtfuse_set_rows_per_item(int rows);
+
+/*
+ * Launch-shape knobs for the autotuner: the most bands one launch (or one
+ * batched table entry) of the forward handles (fwd) and of the adjoint
+ * (bwd).  A scene with more bands is run in balanced chunks of at most that
+ * many (the forward reads PAN once per chunk; later adjoint chunks add into
+ * grad_pan).  0 (the default) keeps the library's choice: 8 bands, 6 on rows
+ * off the 16-byte grid.  With a bwd knob set, or a rows knob
+ * (dwtfuse_set_rows_per_item), the batched adjoint uses it too.  Fused values
+ * do not depend on the forward knob; grad_pan sums its chunks in order, so
+ * the adjoint knob can change its last bits.  Process-wide; values outside
+ * [0, 8] are DWTFUSE_EINVAL.
+ */
+int dwtfuse_set_band_chunks(int fwd, int bwd);
 
 /*
  * Test hook for the metric passes' bounded waits (no counterpart in the

@@ -18,11 +18,17 @@ def fuse(pan: torch.Tensor, ms, wavelet: int, f32: bool = True, u8: bool = False
 
     pan: (H, W) uint8 or float32 CUDA tensor; ms: (B, H/2, W/2) tensor or list
     of (H/2, W/2) tensors of the same dtype.  Returns (out_f32, out_u8), each a
-    (B, H, W) tensor or None.
+    (B, H, W) tensor or None.  Runs in the launch shape the autotuner cached
+    for this scene class (tune.tune_fuse), if there is one.
     """
+    from . import tune
     bands = _C._bands(ms)
     H, W = pan.shape
     out_f = torch.empty((len(bands), H, W), dtype=torch.float32, device=pan.device) if f32 else None
     out_u = torch.empty((len(bands), H, W), dtype=torch.uint8, device=pan.device) if u8 else None
-    _C.dwtfuse_fuse(pan, bands, wavelet, out_f, out_u, stream)
+    # The launch shape tune.tune_fuse cached for this scene class, if any (no tuning here).
+    key = tune.current_device_key() + "|" + tune.fuse_class(
+        H, W, len(bands), wavelet, _C._dtype_code(pan, "pan"), ("f" if f32 else "") + ("u" if u8 else ""))
+    with tune.using(tune.cached(key)):
+        _C.dwtfuse_fuse(pan, bands, wavelet, out_f, out_u, stream)
     return out_f, out_u

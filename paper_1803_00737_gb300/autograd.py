@@ -9,14 +9,25 @@ from __future__ import annotations
 
 import torch
 
-from . import _C
+from . import _C, tune
+
+
+def _shape(key: str, run_tuner) -> "tune.LaunchShape | None":
+    """The tuned launch shape for a key: from the cache, else tuned now (once
+    per machine and shape class), else None when tuning is not allowed (inside
+    a graph capture, or DWTFUSE_AUTOTUNE=0)."""
+    got = tune.cached(key)
+    if got is None and tune.tuning_allowed():
+        got = run_tuner()
+    return got
 
 
 def fuse_batch(P: torch.Tensor, M: torch.Tensor, wavelet: int, out: torch.Tensor) -> None:
     """Float forward of a batch: P (N, H, W), M (N, B, H/2, W/2), out (N, B, H, W).
     Batches go through the batched persistent kernel (one launch per up to
-    DWTFUSE_MAX_SCENES scenes, its workspace from torch's allocator); a single
-    scene, or more than 8 bands, through dwtfuse_fuse."""
+    DWTFUSE_MAX_SCENES scenes, its workspace from torch's allocator) in the
+    launch shape the autotuner picked for this batch shape; a single scene, or
+    more than 8 bands, through dwtfuse_fuse."""
     N, B = M.shape[0], M.shape[1]
     if N == 1 or B > 8:
         for i in range(N):
@@ -24,23 +35,35 @@ def fuse_batch(P: torch.Tensor, M: torch.Tensor, wavelet: int, out: torch.Tensor
         return
     ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=P.device)
     for i0 in range(0, N, _C.MAX_SCENES):
-        scenes = [_C.make_scene(P[i], M[i], wavelet, out[i], None) for i in range(i0, min(N, i0 + _C.MAX_SCENES))]
-        _C.dwtfuse_fuse_batched(scenes, ws)
+        idx = range(i0, min(N, i0 + _C.MAX_SCENES))
+        scenes = [_C.make_scene(P[i], M[i], wavelet, out[i], None) for i in idx]
+        specs = [(P.shape[1], P.shape[2], B, wavelet)] * len(idx)
+        shape = _shape(tune.current_device_key() + "|" + tune.batched_class(specs),
+                       lambda: tune.tune_batched(scenes, specs, ws))
+        rows, blocks = (shape.rows_per_item, shape.blocks_per_sm) if shape else (0, 0)
+        with tune.using(tune.LaunchShape(0, 0, shape.fwd_chunk, 0) if shape else None):
+            _C.dwtfuse_fuse_batched(scenes, ws, rows, blocks)
 
 
 def fuse_batch_backward(g: torch.Tensor, wavelet: int, gp: torch.Tensor, gm: torch.Tensor) -> None:
     """Adjoint of a batch: g (N, B, H, W) into gp (N, H, W) and gm (N, B, H/2, W/2).
-    Batches go through the batched adjoint (one persistent launch per chunk of
-    4 bands over up to DWTFUSE_MAX_SCENES scenes); a single scene through
+    Batches go through the batched adjoint (one persistent launch per band
+    chunk over up to DWTFUSE_MAX_SCENES scenes) in the launch shape the
+    autotuner picked for this batch shape; a single scene through
     dwtfuse_fuse_backward."""
     N = g.shape[0]
     if N == 1:
         _C.dwtfuse_fuse_backward(g[0], wavelet, gp[0], gm[0])
         return
+    N_, B, H, W = g.shape
+    shape = _shape(tune.current_device_key() + "|" + tune.backward_class(N, H, W, B, wavelet),
+                   lambda: tune.tune_backward(g, wavelet, gp, gm))
     ws = torch.empty(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=g.device)
-    for i0 in range(0, N, _C.MAX_SCENES):
-        scenes = [_C.make_grad_scene(g[i], wavelet, gp[i], gm[i]) for i in range(i0, min(N, i0 + _C.MAX_SCENES))]
-        _C.dwtfuse_fuse_backward_batched(scenes, ws)
+    with tune.using(shape):
+        for i0 in range(0, N, _C.MAX_SCENES):
+            scenes = [_C.make_grad_scene(g[i], wavelet, gp[i], gm[i])
+                      for i in range(i0, min(N, i0 + _C.MAX_SCENES))]
+            _C.dwtfuse_fuse_backward_batched(scenes, ws)
 
 
 class DWTFuseFn(torch.autograd.Function):

@@ -18,6 +18,8 @@ std::unordered_map<const void *, int> g_occ;
 std::map<std::pair<int, const void *>, int> g_occ_smem;
 std::unordered_map<int, int> g_sms;
 std::atomic<int> g_rows{0};  // 0: balanced_rows() per launch
+std::atomic<int> g_fwd_chunk{0};  // dwtfuse_set_band_chunks (0: library default)
+std::atomic<int> g_bwd_chunk{0};
 std::atomic<int> g_metric_wait_test{0};  // dwtfuse_set_metric_wait_test
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 }  // namespace
@@ -88,6 +90,8 @@ cudaError_t sm_count(int *out) {
 }
 
 int rows_per_item() { return g_rows.load(std::memory_order_relaxed); }
+int fwd_band_chunk() { return g_fwd_chunk.load(std::memory_order_relaxed); }
+int bwd_band_chunk() { return g_bwd_chunk.load(std::memory_order_relaxed); }
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DWTFUSE_OK;
@@ -154,6 +158,7 @@ int make_scene(const void *pan, const void *const *ms, int bands, int64_t H, int
 int build_batch_table(const dwtfuse_scene *scenes, int n, int rows_per_item, BatchTable *t) {
     std::memset(t, 0, sizeof *t);
     t->R = rows_per_item > 0 ? rows_per_item : kDefaultRows;
+    const int knob = fwd_band_chunk();
     int64_t acc = 0;
     int k = 0;
     for (int i = 0; i < n; ++i) {
@@ -165,15 +170,23 @@ int build_batch_table(const dwtfuse_scene *scenes, int n, int rows_per_item, Bat
         if (st != DWTFUSE_OK) return st;
         const ItemGrid g = item_grid(d.H, d.W, t->R);
         const bool alt = sa.alt && !sa.a4;
-        const bool split = alt && sa.bands > kBatchAltMaxBands && (n - i - 1) + k + 2 <= kMaxScenes;
-        if (alt && sa.bands > kBatchAltMaxBands && !split) sa.alt = 0;
-        const int parts = split ? 2 : 1;
+        // Band groups per entry: at most kBatchAltMaxBands on shifted rows, at
+        // most the band-chunk knob when it is set; balanced groups.
+        int cap = alt ? kBatchAltMaxBands : kBatchMaxBands;
+        if (knob > 0 && knob < cap) cap = knob;
+        int parts = (sa.bands + cap - 1) / cap;
+        if (parts > 1 && (n - i - 1) + k + parts > kMaxScenes) {
+            // no room in the table: one entry (shifted rows then take the pair body)
+            parts = 1;
+            if (alt && sa.bands > kBatchAltMaxBands) sa.alt = 0;
+        }
+        const int per = (sa.bands + parts - 1) / parts;
         const int64_t HW = d.H * d.W;
         for (int p = 0; p < parts; ++p) {
             SceneArgs e = sa;
-            if (split) {
-                const int b0 = p == 0 ? 0 : (sa.bands + 1) / 2;
-                const int nb = p == 0 ? (sa.bands + 1) / 2 : sa.bands - (sa.bands + 1) / 2;
+            if (parts > 1) {
+                const int b0 = p * per;
+                const int nb = sa.bands - b0 < per ? sa.bands - b0 : per;
                 for (int b = 0; b < kMaxBands; ++b) e.ms[b] = b < nb ? sa.ms[b0 + b] : nullptr;
                 e.bands = nb;
                 if (e.out_f32) e.out_f32 += (int64_t)b0 * HW;
@@ -224,6 +237,13 @@ int dwtfuse_set_metric_wait_test(int on) {
 int dwtfuse_set_rows_per_item(int rows) {
     if (rows < 0 || rows > 4096) return DWTFUSE_EINVAL;
     g_rows.store(rows, std::memory_order_relaxed);
+    return DWTFUSE_OK;
+}
+
+int dwtfuse_set_band_chunks(int fwd, int bwd) {
+    if (fwd < 0 || fwd > kChunkBands || bwd < 0 || bwd > kChunkBands) return DWTFUSE_EINVAL;
+    g_fwd_chunk.store(fwd, std::memory_order_relaxed);
+    g_bwd_chunk.store(bwd, std::memory_order_relaxed);
     return DWTFUSE_OK;
 }
 

@@ -18,7 +18,13 @@
 // Haar loads two coefficient rows' inputs per step (16384^2: forward 0.32 ->
 // 0.23 ms, inverse 0.37 -> 0.35 ms; the forward only with streaming stores,
 // with plain stores the two-row body came out slower, 0.46 ms); the same for
-// D4 measured slower (forward 0.29 -> 0.37 ms), so D4 keeps one row per step.
+// D4 measured slower (forward 0.29 -> 0.37 ms), so D4 keeps one row per step
+// and instead loads the next step's rows one step ahead.  Both D4 passes were
+// latency-bound (ncu at 8192^2: long-scoreboard stalls 7 and 11 per issue,
+// DRAM 48 % and 55 % of peak): with the prefetch and four CTAs per SM for the
+// forward (60 registers, uint8 rows kept as raw words) and three for the
+// inverse (80 registers, 32 bytes of spill), 16384^2 runs at forward 0.29 ->
+// 0.27 ms and inverse 0.45 -> 0.39 ms (two CTAs per SM: 0.44 ms).
 #include "fuse_tile.cuh"
 #include "launch.h"
 
@@ -56,6 +62,41 @@ __device__ __forceinline__ void d4_row_ad(const float *v, float *ra, float *rd) 
         ra[j] = fmaf(kH3, s[3], fmaf(kH2, s[2], fmaf(kH1, s[1], kH0 * s[0])));
         rd[j] = fmaf(kG3, s[3], fmaf(kG2, s[2], fmaf(kG1, s[1], kG0 * s[0])));
     }
+}
+
+// Raw uint8 words of one image row for a lane's D4 taps (pixels x-2..x+5,
+// periodic): the pair at x-2, the 4 pixels at x (one word on the vector path,
+// else two pairs), the pair at x+4.
+struct Raw8 {
+    uint32_t l, m0, m1, r;
+};
+
+template <typename T>
+__device__ __forceinline__ Raw8 load_raw8(const T *row, const LaneCols &c, bool a4) {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(row);
+    Raw8 w;
+    w.l = __ldg(reinterpret_cast<const unsigned short *>(p + c.cm));
+    if (a4) {
+        w.m0 = __ldg(reinterpret_cast<const unsigned int *>(p + c.x));
+        w.m1 = 0;
+    } else {
+        w.m0 = __ldg(reinterpret_cast<const unsigned short *>(p + c.x));
+        w.m1 = __ldg(reinterpret_cast<const unsigned short *>(p + c.c2));
+    }
+    w.r = __ldg(reinterpret_cast<const unsigned short *>(p + c.c4));
+    return w;
+}
+
+__device__ __forceinline__ void unpack_raw8(const Raw8 &w, bool a4, float *v) {
+    v[0] = byte_f(w.l, 0);
+    v[1] = byte_f(w.l, 1);
+    const uint32_t mid = a4 ? w.m0 : (w.m0 | (w.m1 << 16));
+    v[2] = byte_f(mid, 0);
+    v[3] = byte_f(mid, 1);
+    v[4] = byte_f(mid, 2);
+    v[5] = byte_f(mid, 3);
+    v[6] = byte_f(w.r, 0);
+    v[7] = byte_f(w.r, 1);
 }
 
 template <typename T, int WAV>
@@ -105,10 +146,28 @@ __device__ __forceinline__ void dwt2_item(const DwtArgs &s, int64_t x0, int64_t 
         load_row8(img + (2 * m_s + 1) * W, c, a4, v);
         d4_row_ad(v, a1, d1);
     }
+    // uint8 images: the raw words of the next step's two rows are loaded one
+    // step ahead (a few registers), so a warp's loads overlap its arithmetic.
+    constexpr bool kPrefetch = sizeof(T) == 1;
+    Raw8 na, nb;
+    if constexpr (kPrefetch) {
+        na = load_raw8(img + wrap(2 * m_s + 2, H) * W, c, a4);
+        nb = load_raw8(img + wrap(2 * m_s + 3, H) * W, c, a4);
+    }
     for (int64_t m = m_s; m < m_e; ++m) {
         float va[8], vb[8];
-        load_row8(img + wrap(2 * m + 2, H) * W, c, a4, va);
-        load_row8(img + wrap(2 * m + 3, H) * W, c, a4, vb);
+        if constexpr (kPrefetch) {
+            const Raw8 ra = na, rb = nb;
+            if (m + 1 < m_e) {
+                na = load_raw8(img + wrap(2 * m + 4, H) * W, c, a4);
+                nb = load_raw8(img + wrap(2 * m + 5, H) * W, c, a4);
+            }
+            unpack_raw8(ra, a4, va);
+            unpack_raw8(rb, a4, vb);
+        } else {
+            load_row8(img + wrap(2 * m + 2, H) * W, c, a4, va);
+            load_row8(img + wrap(2 * m + 3, H) * W, c, a4, vb);
+        }
         float a2[2], d2[2], a3[2], d3[2];
         d4_row_ad(va, a2, d2);
         d4_row_ad(vb, a3, d3);
@@ -204,12 +263,26 @@ __device__ __forceinline__ void idwt2_item(const DwtArgs &s, int64_t x0, int64_t
         load_coef3(Z + (H2 + mp) * W + W2, c, G);
         d4_row_syn(L, G, rbp);
     }
+    // The next row's 12 coefficients are loaded one step ahead (the kernel
+    // runs two CTAs per SM at its register count either way), so a warp's
+    // loads overlap its arithmetic.
+    float nL0[3], nG0[3], nL1[3], nG1[3];
+    load_coef3(Z + m_s * W, c, nL0);
+    load_coef3(Z + m_s * W + W2, c, nG0);
+    load_coef3(Z + (H2 + m_s) * W, c, nL1);
+    load_coef3(Z + (H2 + m_s) * W + W2, c, nG1);
     for (int64_t m = m_s; m < m_e; ++m) {
         float L0[3], G0[3], L1[3], G1[3];
-        load_coef3(Z + m * W, c, L0);
-        load_coef3(Z + m * W + W2, c, G0);
-        load_coef3(Z + (H2 + m) * W, c, L1);
-        load_coef3(Z + (H2 + m) * W + W2, c, G1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            L0[k] = nL0[k]; G0[k] = nG0[k]; L1[k] = nL1[k]; G1[k] = nG1[k];
+        }
+        if (m + 1 < m_e) {
+            load_coef3(Z + (m + 1) * W, c, nL0);
+            load_coef3(Z + (m + 1) * W + W2, c, nG0);
+            load_coef3(Z + (H2 + m + 1) * W, c, nL1);
+            load_coef3(Z + (H2 + m + 1) * W + W2, c, nG1);
+        }
         float ra[4], rb[4];
         d4_row_syn(L0, G0, ra);
         d4_row_syn(L1, G1, rb);
@@ -229,8 +302,10 @@ __device__ __forceinline__ void idwt2_item(const DwtArgs &s, int64_t x0, int64_t
     }
 }
 
+// Forward instances run four CTAs per SM (at most 64 registers), the
+// inverse three (at most 85).
 template <typename T, int WAV, bool INV>
-__global__ void __launch_bounds__(kDwtThreads, 2)
+__global__ void __launch_bounds__(kDwtThreads, INV ? 3 : 4)
 dwt2_kernel(const __grid_constant__ DwtArgs s, int64_t strips_x, int64_t items, int R) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * kDwtWarps;

@@ -484,11 +484,16 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
                                          cudaStream_t stream) {
     static thread_local BwdBatchTable t;  // ~28 KB: kept off the stack
     static thread_local BwdArgs scenes[kMaxScenes];
+    // Band chunk: 8, or the autotuner's band-chunk knob; rows per item: the
+    // default, or the rows knob.
+    const int knob = bwd_band_chunk();
+    const int cw = knob > 0 && knob < kBwdChunk ? knob : kBwdChunk;
+    const int rows = rows_per_item();
     int max_chunks = 0;
     for (int i = 0; i < n; ++i) {
         scenes[i] = make_bwd_args(in[i].grad_out, in[i].bands, in[i].H, in[i].W, in[i].wavelet, in[i].grad_pan,
                                   in[i].grad_ms);
-        const int nc = (scenes[i].bands + kBwdChunk - 1) / kBwdChunk;
+        const int nc = (scenes[i].bands + cw - 1) / cw;
         max_chunks = nc > max_chunks ? nc : max_chunks;
     }
     int sms = 0;
@@ -498,13 +503,13 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
         for (int kind = 0; kind < 4; ++kind) {  // (1-4 bands, 5-8 bands) x (Haar, D4)
             const int wide = kind >> 1, wav = kind & 1;
             std::memset(&t, 0, sizeof t);
-            t.R = kDefaultRows;
+            t.R = rows > 0 ? rows : kDefaultRows;
             int64_t acc = 0;
             int k = 0;
             for (int i = 0; i < n; ++i) {
-                const int b0 = chunk * kBwdChunk;
+                const int b0 = chunk * cw;
                 const int rest = scenes[i].bands - b0;
-                const int nb = rest < kBwdChunk ? rest : kBwdChunk;
+                const int nb = rest < cw ? rest : cw;
                 if (nb <= 0 || (nb > 4) != (wide != 0) || scenes[i].wavelet != wav) continue;
                 const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
                 t.scenes[k] = scenes[i];
@@ -547,8 +552,10 @@ cudaError_t launch_fuse_backward(const float *g, int bands, int64_t H, int64_t W
     int sms = 0;
     cudaError_t e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    for (int b0 = 0; b0 < bands; b0 += kBwdChunk) {
-        const int nb = bands - b0 < kBwdChunk ? bands - b0 : kBwdChunk;
+    const int knob = bwd_band_chunk();
+    const int cw = knob > 0 && knob < kBwdChunk ? knob : kBwdChunk;
+    for (int b0 = 0; b0 < bands; b0 += cw) {
+        const int nb = bands - b0 < cw ? bands - b0 : cw;
         const void *fn = wavelet == 0 ? bwd_fn_nb<0>(nb, s.alt != 0) : bwd_fn_nb<1>(nb, s.alt != 0);
         const int threads = bwd_threads(nb), warps = threads / 32;
         int occ = 0;

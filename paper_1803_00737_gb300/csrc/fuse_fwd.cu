@@ -114,11 +114,14 @@ void *fwd_kernel_ptr(bool f32, int wav, int nb, bool alt) {
 
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream) {
     // Bands go in chunks of up to 8; the shifted-row instance (W % 4 == 2)
-    // holds more live registers per band and takes balanced chunks of <= 6.
+    // holds more live registers per band and takes balanced chunks of <= 6;
+    // a band-chunk knob (autotuner) caps both, in balanced chunks.
     const bool alt = s.alt != 0 && s.a4 == 0;
-    const int cap = alt ? kAltMaxBands : kChunkBands;
+    const int knob = fwd_band_chunk();
+    int cap = alt ? kAltMaxBands : kChunkBands;
+    if (knob > 0 && knob < cap) cap = knob;
     const int nchunks = (s.bands + cap - 1) / cap;
-    const int chunk = alt ? (s.bands + nchunks - 1) / nchunks : kChunkBands;
+    const int chunk = (alt || knob > 0) ? (s.bands + nchunks - 1) / nchunks : kChunkBands;
     for (int b0 = 0; b0 < s.bands; b0 += chunk) {
         const int nb = s.bands - b0 < chunk ? s.bands - b0 : chunk;
         void *fn = fwd_kernel_ptr(s.in_f32 != 0, s.wavelet, nb, alt);

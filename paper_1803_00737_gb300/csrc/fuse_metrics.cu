@@ -8,7 +8,8 @@
 //
 // Work item: a warp strip of 128 PAN columns (four windows side by side, 8
 // lanes each) over R MS rows, R a multiple of 16 and items starting on window
-// rows.  Every two MS rows (4 PAN rows) the warp parks its uint8 pixels,
+// rows.  Every two MS rows (4 PAN rows; every MS row for 8 bands) the warp
+// parks its uint8 pixels,
 // the matching PAN pixels and the MS reference values in a per-warp shared
 // tile (a private spill area: each lane reads back only its own words, so the
 // fusion's registers are free again) and adds their sums into per-lane
@@ -36,9 +37,12 @@ struct FmLayout {
     static constexpr int K = NB + 1;                  // images: NB bands, then PAN
     static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs (b < c), then band-PAN pairs
     static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
+    // MS rows parked before they are scored: 2, or 1 for 8 bands, so that two
+    // CTAs still fit an SM's shared memory.
+    static constexpr int SR = NB <= 7 ? 2 : 1;
     // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
-    static constexpr int kTile = K * 4 * 32;          // uint8 words of 4 PAN rows: bands, PAN
-    static constexpr int kRep = NB * 2 * 32;          // MS reference words of 2 MS rows
+    static constexpr int kTile = K * 2 * SR * 32;     // uint8 words of 2 SR PAN rows: bands, PAN
+    static constexpr int kRep = NB * SR * 32;         // MS reference words of SR MS rows
     static constexpr int kSums = NS * 32;
     static constexpr int kQ = 4 * P;                  // float Q sums per window position
     static constexpr int kWords = (kTile + kRep + kSums + kQ + 1) & ~1;
@@ -61,7 +65,7 @@ template <int NB>
 struct MetricEmit {
     using L = FmLayout<NB>;
     static constexpr bool kAllLanes = true;
-    static constexpr int K = L::K, P = L::P, NS = L::NS;
+    static constexpr int K = L::K, P = L::P, NS = L::NS, SR = L::SR;
     const SceneArgs &s;
     const LaneCols &c;
     uint32_t *tile, *rep;
@@ -78,11 +82,11 @@ struct MetricEmit {
                                          float mn1) const {
         const uint32_t w0 = pack4(f2u8(v0[0]), f2u8(v0[1]), f2u8(v0[2]), f2u8(v0[3]));
         const uint32_t w1 = pack4(f2u8(v1[0]), f2u8(v1[1]), f2u8(v1[2]), f2u8(v1[3]));
-        const int r = (int)((m - m_s) & 1);
-        tile[(b * 4 + 2 * r) * 32 + lane] = w0;
-        tile[(b * 4 + 2 * r + 1) * 32 + lane] = w1;
+        const int r = (int)((m - m_s) & (SR - 1));  // SR is 1 or 2
+        tile[(b * 2 * SR + 2 * r) * 32 + lane] = w0;
+        tile[(b * 2 * SR + 2 * r + 1) * 32 + lane] = w1;
         // ERGAS reference: MS(m, n), MS(m, n+1) each repeated over 2 PAN columns.
-        rep[(b * 2 + r) * 32 + lane] = __byte_perm(f2u8(mn), f2u8(mn1), 0x4400u);
+        rep[(b * SR + r) * 32 + lane] = __byte_perm(f2u8(mn), f2u8(mn1), 0x4400u);
         const int64_t HW = s.H * s.W;
         const int64_t o0 = (int64_t)b * HW + (2 * m) * s.W + c.x, o1 = o0 + s.W;
         if (alt) {
@@ -122,9 +126,73 @@ struct MetricEmit {
         }
     }
 
+    // Pair sums [LO, HI) of the tile's first `nr` PAN rows into this lane's
+    // slots (7-8 bands: the 28-36 pair sums are formed in two passes over the
+    // parked words, so that fewer of them are live next to the walker's state).
+    template <int LO, int HI>
+    __device__ __forceinline__ void pair_sums(int nr) const {
+        int sxy[HI - LO];
+#pragma unroll
+        for (int k = 0; k < HI - LO; ++k) sxy[k] = 0;
+        for (int r = 0; r < nr; ++r) {
+            int v[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = (int)(tile[(k * 2 * SR + r) * 32 + lane] ^ 0x80808080u);
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2) {
+                    const int q = pair_index(NB, b, c2);
+                    if (c2 > b && q >= LO && q < HI) sxy[q - LO] = __dp4a(v[b], v[c2], sxy[q - LO]);
+                }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const int q = NB * (NB - 1) / 2 + b;
+                if (q >= LO && q < HI) sxy[q - LO] = __dp4a(v[b], v[NB], sxy[q - LO]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < HI - LO; ++k) sums[(2 * K + LO + k) * 32 + lane] += sxy[k];
+    }
+
     // Sums of the tile's first `nr` PAN rows into this lane's slots.  qon: the
     // lane's window is inside the image (window sums wanted).
     __device__ __forceinline__ void score(int nr, bool qon) const {
+        if constexpr (NB >= 7) {
+            int s1[K], s2[K], se[NB];
+#pragma unroll
+            for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) se[b] = 0;
+            for (int r = 0; r < nr; ++r) {
+                uint32_t f[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) f[k] = tile[(k * 2 * SR + r) * 32 + lane];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const uint32_t d = __vabsdiffu4(f[b], rep[(b * SR + (r >> 1)) * 32 + lane]) & keep;
+                    se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int v = (int)(f[k] ^ 0x80808080u);
+                    s1[k] = __dp4a(v, 0x01010101, s1[k]);
+                    s2[k] = __dp4a(v, v, s2[k]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) se64[b * 32 + lane] += se[b];
+            if (qon) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    sums[k * 32 + lane] += s1[k];
+                    sums[(K + k) * 32 + lane] += s2[k];
+                }
+                pair_sums<0, P / 2>(nr);
+                pair_sums<P / 2, P>(nr);
+            }
+            return;
+        }
         int s1[K], s2[K], sxy[P], se[NB];
 #pragma unroll
         for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
@@ -135,10 +203,10 @@ struct MetricEmit {
         for (int r = 0; r < nr; ++r) {
             uint32_t f[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) f[k] = tile[(k * 4 + r) * 32 + lane];
+            for (int k = 0; k < K; ++k) f[k] = tile[(k * 2 * SR + r) * 32 + lane];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const uint32_t d = __vabsdiffu4(f[b], rep[(b * 2 + (r >> 1)) * 32 + lane]) & keep;
+                const uint32_t d = __vabsdiffu4(f[b], rep[(b * SR + (r >> 1)) * 32 + lane]) & keep;
                 se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
             }
             if (qon) {
@@ -207,11 +275,11 @@ struct MetricEmit {
     }
 
     __device__ __forceinline__ void row_end(int64_t m, const float *pan0, const float *pan1) const {
-        const int r = (int)((m - m_s) & 1);
-        tile[(NB * 4 + 2 * r) * 32 + lane] = pack4(f2u8(pan0[0]), f2u8(pan0[1]), f2u8(pan0[2]), f2u8(pan0[3]));
-        tile[(NB * 4 + 2 * r + 1) * 32 + lane] = pack4(f2u8(pan1[0]), f2u8(pan1[1]), f2u8(pan1[2]), f2u8(pan1[3]));
+        const int r = (int)((m - m_s) & (SR - 1));  // SR is 1 or 2
+        tile[(NB * 2 * SR + 2 * r) * 32 + lane] = pack4(f2u8(pan0[0]), f2u8(pan0[1]), f2u8(pan0[2]), f2u8(pan0[3]));
+        tile[(NB * 2 * SR + 2 * r + 1) * 32 + lane] = pack4(f2u8(pan1[0]), f2u8(pan1[1]), f2u8(pan1[2]), f2u8(pan1[3]));
         const bool last = m + 1 == m_e;
-        if (r == 0 && !last) return;
+        if (r != SR - 1 && !last) return;
         // Rows 2m' .. 2m+1 of the window row starting at PAN row y_win.
         const int64_t y_win = ((2 * m) / 32) * 32;
         const bool row_full = y_win + 32 <= s.H;
@@ -293,6 +361,7 @@ void *fm_kernel_ptr(int wav, int nb, int *smem) {
         *smem = FmLayout<NBV>::kSmem;          \
         return wav ? fm_fn<1, NBV>() : fm_fn<0, NBV>();
         DWTFUSE_FM(1) DWTFUSE_FM(2) DWTFUSE_FM(3) DWTFUSE_FM(4) DWTFUSE_FM(5) DWTFUSE_FM(6)
+        DWTFUSE_FM(7) DWTFUSE_FM(8)
 #undef DWTFUSE_FM
         default: return nullptr;
     }

@@ -58,7 +58,7 @@ struct MetricLaunch {
 
 // Fused forward + PAN-resolution metrics (fuse_metrics.cu): uint8 inputs, a
 // uint8 output, up to this many bands in one launch.
-constexpr int kFuseMetricsMaxBands = 6;
+constexpr int kFuseMetricsMaxBands = 8;
 
 // MS rows per work item that balance the last wave of a grid of `warps`
 // warps: minimises ceil(items / warps) * (R + 1) over R in [16, 64] (the +1
@@ -91,6 +91,12 @@ struct DwtLaunch {
     int32_t pairs;     // coefficient pairs 8-byte aligned in both halves
     int32_t rows;      // MS rows per work item (0 = balanced)
 };
+
+// Launch-shape knobs (dwtfuse_set_rows_per_item, dwtfuse_set_band_chunks);
+// 0 means the library default.
+int rows_per_item();
+int fwd_band_chunk();
+int bwd_band_chunk();
 
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);

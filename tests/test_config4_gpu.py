@@ -1,7 +1,8 @@
 """Full-size batched forward + backward with metrics: scenes of the 12-scene
 workload (square PAN, sides even in [8192, 32768], 8 MS bands, D4), one at a
-time: batched forward (float32 + uint8), ERGAS/QNR of the uint8 product, and
-the adjoint of a seeded output gradient G.
+time: batched forward (float32 + uint8), ERGAS/QNR of the uint8 product (the
+separate passes, and the forward that scores its product on chip, which
+must agree), and the adjoint of a seeded output gradient G.
 
 Checked per scene, element by element against the oracle's point-wise
 evaluators: the fused bands on two seeded 256 x 256 windows and on the wrap
@@ -48,6 +49,16 @@ def _run_scene(sp, ws, mws):
     _C.dwtfuse_fuse_batched([_C.make_scene(pan, ms, sp.wavelet, out, out8)], ws)
     res = torch.zeros(4, dtype=torch.float64, device=DEV)
     _C.dwtfuse_metrics(out8, ms, pan, mws, res)
+    # The benchmark's form: the forward scoring its uint8 product on chip.  Its
+    # outputs overwrite the batched forward's with the same bits (checked).
+    keep8 = out8.clone()
+    res2 = torch.zeros(4, dtype=torch.float64, device=DEV)
+    _C.dwtfuse_fuse_metrics(pan, ms, sp.wavelet, None, out8, mws, res2)
+    torch.cuda.synchronize()
+    assert torch.equal(keep8, out8)
+    del keep8
+    r1, r2 = res.cpu().numpy(), res2.cpu().numpy()
+    assert r1[0] == r2[0] and np.abs(r1[1:] - r2[1:]).max() <= 1e-6, (r1, r2)
     G = scenegen.target_like((8, H, W), seed=sp.seed + 5, device=DEV)
     gp = torch.empty((H, W), device=DEV)
     gm = torch.empty((8, H // 2, W // 2), device=DEV)

@@ -59,7 +59,8 @@ def agree(a, b):
 # Window-aligned and ragged sizes: W off the 128-column strip grid, W = 2 mod 4,
 # H/2 odd (a last two-row block of one MS row), partial window rows and columns.
 SHAPES = [((64, 64), 3), ((128, 256), 6), ((96, 160), 2), ((130, 258), 4), ((200, 136), 5),
-          ((66, 70), 1), ((192, 1030), 6), ((64, 534), 6), ((98, 610), 3)]
+          ((66, 70), 1), ((192, 1030), 6), ((64, 534), 6), ((98, 610), 3), ((128, 256), 8),
+          ((130, 258), 7), ((192, 1030), 8), ((64, 534), 7), ((98, 612), 8)]
 
 
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
@@ -73,7 +74,8 @@ def test_fused_metrics_equal_separate_calls(wav, shape, B, ws):
 
 
 @pytest.mark.parametrize("wav", [O.HAAR, O.D4])
-@pytest.mark.parametrize("shape,B", [((128, 192), 6), ((130, 258), 3), ((96, 610), 5)])
+@pytest.mark.parametrize("shape,B", [((128, 192), 6), ((130, 258), 3), ((96, 610), 5), ((128, 192), 8),
+                                     ((98, 610), 7)])
 def test_fused_metrics_against_oracle(wav, shape, B, ws):
     pan, ms = scene(*shape, B, seed=3 * sum(shape) + B)
     _, u, r = fused_path(pan, ms, wav, ws, f32=False)
@@ -84,15 +86,22 @@ def test_fused_metrics_against_oracle(wav, shape, B, ws):
     assert np.abs(r[1:] - ref[1:]).max() <= 2e-6, (r, ref)
 
 
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
 @pytest.mark.parametrize("B", [7, 8])
-def test_more_bands_run_the_separate_kernels(B, ws):
-    """Above 6 bands the call runs the forward and the metric passes one
-    after the other; the result is the same as calling them separately."""
-    pan, ms = scene(96, 160, B, seed=B)
-    f1, u1, r1 = fused_path(pan, ms, O.D4, ws)
-    f2, u2, r2 = separate_path(pan, ms, O.D4, ws)
-    assert torch.equal(f1, f2) and torch.equal(u1, u2)
-    assert np.array_equal(r1, r2)
+def test_seven_and_eight_bands_score_on_chip(wav, B, ws):
+    """7 and 8 bands (8 parks one MS row at a time, the pair sums run in two
+    passes): the two-call form accepts them, and the outputs and figures
+    equal the separate calls' (Q sums to 1e-6)."""
+    pan, ms = scene(160, 288, B, seed=B)
+    Bn, (H, W) = ms.shape[0], pan.shape
+    ou = torch.empty((Bn, H, W), dtype=torch.uint8, device=DEV)
+    res = torch.full((4,), float("nan"), dtype=torch.float64, device=DEV)
+    _C.dwtfuse_fuse_and_score(pan, ms, wav, None, ou, ws)
+    _C.dwtfuse_score_finish(ms, pan, ou, ws, res)
+    torch.cuda.synchronize()
+    f2, u2, r2 = separate_path(pan, ms, wav, ws)
+    assert torch.equal(ou, u2)
+    agree(res.cpu().numpy(), r2)
 
 
 def test_float_inputs_run_the_separate_kernels(ws):
@@ -168,10 +177,14 @@ def test_two_call_form(ws):
 
 
 def test_two_call_form_rejects_unsupported(ws):
-    pan, ms = scene(64, 96, 7, seed=2)
-    ou = torch.empty((7, 64, 96), dtype=torch.uint8, device=DEV)
-    with pytest.raises(_C.DwtfuseError):
-        _C.dwtfuse_fuse_and_score(pan, ms, O.D4, None, ou, ws)
+    pan, ms = scene(64, 96, 3, seed=2)
+    ou = torch.empty((3, 64, 96), dtype=torch.uint8, device=DEV)
+    with pytest.raises(_C.DwtfuseError):  # float inputs are scored by the separate passes only
+        _C.dwtfuse_fuse_and_score(pan.float(), ms.float(), O.D4, None, ou, ws)
+    pan9, ms9 = scene(64, 96, 9, seed=2)
+    ou9 = torch.empty((9, 64, 96), dtype=torch.uint8, device=DEV)
+    with pytest.raises(_C.DwtfuseError):  # the metrics take at most 8 bands
+        _C.dwtfuse_fuse_and_score(pan9, ms9, O.D4, None, ou9, ws)
 
 
 def test_benchmark_step_full_size(ws):

@@ -10,11 +10,11 @@ from paper_1803_00737_gb300 import tune
 
 
 def test_pick_fastest_and_ties():
-    c = [tune.LaunchShape(r, 0) for r in (8, 16, 32)]
-    t = {8: 3.0, 16: 1.0, 32: 1.0}
-    best, table = tune.pick(c, lambda s: t[s.rows_per_item])
+    c = [tune.LaunchShape(r, 0, f) for r in (8, 16, 32) for f in (0, 4)]
+    t = {(8, 0): 3.0, (16, 0): 1.0, (32, 0): 1.0, (8, 4): 2.0, (16, 4): 1.5, (32, 4): 1.0}
+    best, table = tune.pick(c, lambda s: t[(s.rows_per_item, s.fwd_chunk)])
     assert best == tune.LaunchShape(16, 0)
-    assert table == {"8x0": 3.0, "16x0": 1.0, "32x0": 1.0}
+    assert table["r16b0f0g0"] == 1.0 and table["r8b0f4g0"] == 2.0 and len(table) == 6
     with pytest.raises(ValueError):
         tune.pick([], lambda s: 0.0)
 
@@ -36,19 +36,21 @@ def test_cache_round_trip_and_reuse(tmp_path):
 
     def run():
         calls.append(1)
-        return tune.LaunchShape(24, 1), {"24x1": 0.5}
+        return tune.LaunchShape(24, 0, 6, 4), {"r24b0f6g4": 0.5}
 
-    assert tune.cached_or_tune("k", run, path) == tune.LaunchShape(24, 1)
-    assert tune.cached_or_tune("k", run, path) == tune.LaunchShape(24, 1)
+    assert tune.cached("k", path) is None
+    assert tune.cached_or_tune("k", run, path) == tune.LaunchShape(24, 0, 6, 4)
+    assert tune.cached_or_tune("k", run, path) == tune.LaunchShape(24, 0, 6, 4)
+    assert tune.cached("k", path) == tune.LaunchShape(24, 0, 6, 4)
     assert len(calls) == 1
     data = json.load(open(path))
-    assert data["entries"]["k"]["times_ms"] == {"24x1": 0.5}
-    assert tune.cached_or_tune("k", run, path, retune=True) == tune.LaunchShape(24, 1)
+    assert data["entries"]["k"]["times_ms"] == {"r24b0f6g4": 0.5}
+    assert tune.cached_or_tune("k", run, path, retune=True) == tune.LaunchShape(24, 0, 6, 4)
     assert len(calls) == 2
 
 
-@pytest.mark.parametrize("content", ["{not json", "[]", '{"version": 2, "entries": {}}',
-                                     '{"version": 1, "entries": {"k": {"rows_per_item": "x"}}}'])
+@pytest.mark.parametrize("content", ["{not json", "[]", '{"version": 1, "entries": {}}',
+                                     '{"version": 2, "entries": {"k": {"rows_per_item": "x"}}}'])
 def test_corrupt_cache_is_rebuilt(tmp_path, content):
     path = tmp_path / "t.json"
     path.write_text(content)
@@ -85,9 +87,51 @@ def test_tuned_batched_launch_matches_default(tmp_path):
     shape = tune.tune_batched(scenes, [(s.H, s.W, s.bands, s.wavelet) for s in specs], ws, reps=1,
                               path=str(tmp_path / "t.json"))
     assert shape.rows_per_item in tune.ROWS and shape.blocks_per_sm in tune.BLOCKS
-    for o in outs:
-        o.fill_(float("nan"))
-    _C.dwtfuse_fuse_batched(scenes, ws, shape.rows_per_item, shape.blocks_per_sm)
-    torch.cuda.synchronize()
-    for a, b in zip(outs, ref):
-        assert torch.equal(a, b)
+    assert shape.fwd_chunk in tune.FWD_CHUNKS
+    # every candidate band chunk gives the default launch's bits
+    for f in tune.FWD_CHUNKS:
+        for o in outs:
+            o.fill_(float("nan"))
+        with tune.using(tune.LaunchShape(0, 0, f, 0)):
+            _C.dwtfuse_fuse_batched(scenes, ws, shape.rows_per_item, shape.blocks_per_sm)
+        torch.cuda.synchronize()
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b), f
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("f,g", [(4, 4), (6, 0), (3, 2)])
+def test_band_chunk_knobs_keep_results(f, g):
+    """The forward is bit-identical for any band chunk; the adjoint's grad_MS
+    too, and grad_PAN (chunks added in order) within FP32 rounding."""
+    import torch
+
+    import scenegen
+    from paper_1803_00737_gb300 import _C
+    for wav, (H, W), B in [(1, (64, 136), 8), (0, (66, 258), 7), (1, (130, 250), 6)]:
+        pan, ms = scenegen.make_scene(H, W, B, seed=H)
+        pan, ms = pan.cuda(), ms.cuda()
+        ref = torch.empty((B, H, W), device="cuda")
+        _C.dwtfuse_fuse(pan, ms, wav, ref, None)
+        G = scenegen.target_like((B, H, W), seed=3, device="cuda")
+        gp0, gm0 = torch.empty((H, W), device="cuda"), torch.empty((B, H // 2, W // 2), device="cuda")
+        _C.dwtfuse_fuse_backward(G, wav, gp0, gm0)
+        with tune.using(tune.LaunchShape(0, 0, f, g)):
+            got = torch.empty_like(ref)
+            _C.dwtfuse_fuse(pan, ms, wav, got, None)
+            gp, gm = torch.empty_like(gp0), torch.empty_like(gm0)
+            _C.dwtfuse_fuse_backward(G, wav, gp, gm)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+        assert torch.equal(gm, gm0)
+        assert (gp - gp0).abs().max().item() <= 1e-5 * max(1.0, gp0.abs().max().item())
+
+
+def test_knob_validation():
+    pytest.importorskip("torch")
+    from paper_1803_00737_gb300 import _C
+    L = _C.lib()
+    assert L.dwtfuse_set_band_chunks(0, 0) == _C.OK
+    for f, g in [(-1, 0), (0, 9), (9, 0)]:
+        assert L.dwtfuse_set_band_chunks(f, g) == _C.EINVAL
+    assert L.dwtfuse_set_band_chunks(0, 0) == _C.OK
