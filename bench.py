@@ -574,6 +574,8 @@ def measure_transforms(args, dev, peak: float) -> dict:
     res = {"workload": f"PAN {S}x{S}: uint8 image -> float coefficients (dwt2), float coefficients "
                        "-> float image (idwt2)"}
     for wav, name in ((1, "d4"), (0, "haar")):
+        _C.dwtfuse_dwt2(img, wav, Z)  # first launches (module load, occupancy query) stay untimed
+        _C.dwtfuse_idwt2(Z, wav, out)
         t_f = _time_ms(lambda: _C.dwtfuse_dwt2(img, wav, Z), max(3, args.form_reps), stream) / 1e3
         t_i = _time_ms(lambda: _C.dwtfuse_idwt2(Z, wav, out), max(3, args.form_reps), stream) / 1e3
         px = S * S
