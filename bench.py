@@ -748,6 +748,9 @@ def run_case(args) -> None:
     bld.build()
     dev = "cuda"
     H, W, B = args.side, args.width or args.side, args.bands
+    if args.rows or args.fwd_chunk or args.bwd_chunk:  # launch-shape knobs for this case
+        from paper_1803_00737_gb300 import tune
+        tune.apply(tune.LaunchShape(args.rows, 0, args.fwd_chunk, args.bwd_chunk))
     pan, ms = scenegen.make_scene(H, W, B, seed=0, blob_scale=BLOB_SCALE, device=dev)
     if args.case == "metrics":
         fused = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
@@ -804,6 +807,7 @@ def run_case(args) -> None:
     torch.cuda.synchronize()
     ms_call = e0.elapsed_time(e1) / max(1, args.steps)
     print(json.dumps({"case": args.case, "H": H, "W": W, "bands": B, "calls": args.steps, "ms": ms_call,
+                      "knobs": {"rows": args.rows, "fwd_chunk": args.fwd_chunk, "bwd_chunk": args.bwd_chunk},
                       "algorithmic_GBps": nbytes / (ms_call / 1e3) / 1e9}))
 
 
@@ -829,6 +833,9 @@ def main() -> None:
                     help="time one library call alone at --side x --width with --bands (profiling aid)")
     ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
     ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")
+    ap.add_argument("--rows", type=int, default=0, help="rows-per-item knob of a --case run (0: default)")
+    ap.add_argument("--fwd-chunk", type=int, default=0, help="forward band-chunk knob of a --case run")
+    ap.add_argument("--bwd-chunk", type=int, default=0, help="adjoint band-chunk knob of a --case run")
     args = ap.parse_args()
     if args.case:
         run_case(args)

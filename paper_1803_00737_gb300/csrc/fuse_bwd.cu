@@ -53,7 +53,7 @@ struct BwdArgs {
     int32_t alt;                  // W % 4 == 2 with 16-byte aligned g / gpan: shifted odd rows
     int32_t wavelet;              // 0 Haar, 1 D4
     int32_t b0;                   // first band of the chunk (batched tables)
-    int32_t pad_;
+    int32_t nbc;                  // bands of the chunk (batched tables)
 };
 
 // Scene table of one launch of the batched backward (band chunk b0 of n scenes).
@@ -398,7 +398,7 @@ fuse_bwd_batched_kernel(const __grid_constant__ BwdBatchTable t, unsigned long l
         const int64_t m_s = sy * t.R;
         const int64_t m_e = min(m_s + (int64_t)t.R, s.H >> 1);
         // the table holds a scene here only if its chunk has 1-4 (5-8 when WIDE) bands
-        const int b0 = s.b0, nb = min(s.bands - b0, WIDE ? kBwdChunk : kBwdGroup);
+        const int b0 = s.b0, nb = s.nbc;
         const bool acc = b0 > 0, alt = s.alt != 0;
         const int64_t x0 = sx * kWarpCols;
 #define DWTFUSE_BWD_CASE(NBV)                                                                 \
@@ -514,6 +514,7 @@ cudaError_t launch_fuse_backward_batched(const dwtfuse_grad_scene *in, int n, un
                 const ItemGrid g = item_grid(scenes[i].H, scenes[i].W, t.R);
                 t.scenes[k] = scenes[i];
                 t.scenes[k].b0 = b0;
+                t.scenes[k].nbc = nb;
                 t.item_start[k] = acc;
                 t.strips_x[k] = g.strips_x;
                 acc += g.items;
