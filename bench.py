@@ -752,6 +752,7 @@ def run_case(args) -> None:
         from paper_1803_00737_gb300 import tune
         tune.apply(tune.LaunchShape(args.rows, 0, args.fwd_chunk, args.bwd_chunk))
     pan, ms = scenegen.make_scene(H, W, B, seed=0, blob_scale=BLOB_SCALE, device=dev)
+    extra = {}
     if args.case == "metrics":
         fused = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
         _C.dwtfuse_fuse(pan, ms, WAVELET, None, fused)
@@ -790,6 +791,10 @@ def run_case(args) -> None:
             for (y0, y1, ps, mss), o in zip(slabs, outs):
                 _C.dwtfuse_fuse_rows(ps, mss, WAVELET, H, y0, y1, o, None)
         nbytes = H * W * (1.0 + B * (0.25 + 4.0))
+        whole = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+        _C.dwtfuse_fuse(pan, ms, WAVELET, whole, None)
+        extra["whole_scene_ms"] = _time_ms(lambda: _C.dwtfuse_fuse(pan, ms, WAVELET, whole, None),
+                                           args.steps, torch.cuda.current_stream())
     else:  # backward
         g = scenegen.target_like((B, H, W), seed=1000, device=dev)
         gp = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -808,7 +813,7 @@ def run_case(args) -> None:
     ms_call = e0.elapsed_time(e1) / max(1, args.steps)
     print(json.dumps({"case": args.case, "H": H, "W": W, "bands": B, "calls": args.steps, "ms": ms_call,
                       "knobs": {"rows": args.rows, "fwd_chunk": args.fwd_chunk, "bwd_chunk": args.bwd_chunk},
-                      "algorithmic_GBps": nbytes / (ms_call / 1e3) / 1e9}))
+                      "algorithmic_GBps": nbytes / (ms_call / 1e3) / 1e9, **extra}))
 
 
 def main() -> None:

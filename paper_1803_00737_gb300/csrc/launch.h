@@ -15,6 +15,7 @@ constexpr int kBatchAltMaxBands = 6;  // bands of the batched shifted-row (W % 4
 constexpr int kMaxScenes = 128;    // scenes per batched launch
 constexpr int kDefaultRows = 32;   // MS rows per warp work item (batched default)
 constexpr size_t kQueueBytes = 16; // queue counter (8) + status word (4) + pad
+constexpr int kStagedMaxBands = 6; // bands per launch of the staged forward (fuse_staged.cu)
 
 // Scene table of a batched launch.  It travels by value in the kernel
 // parameter block (< 32 KB), so a captured graph owns its own copy.
@@ -127,5 +128,11 @@ constexpr int64_t kMetricStatusSlot = 5;  // int: DWTFUSE_OK, or DWTFUSE_ETIMEOU
 constexpr int64_t kMetricPanPartialOffset = 8;
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream);
+
+// Staged single-scene forward (fuse_staged.cu): taken for rows on the 16-byte
+// grid with a float output, at most kStagedMaxBands bands, and a last CTA
+// strip at least 7/8 full.
+bool fuse_staged_applies(const SceneArgs &s);
+cudaError_t launch_fuse_staged(const SceneArgs &s, int R, cudaStream_t stream);
 
 }  // namespace dwtfuse

@@ -138,3 +138,33 @@ def test_batched_band_groups_and_table_capacity():
             torch.cuda.synchronize()
             assert torch.equal(out, f), sp
             assert torch.equal(out8, u), sp
+
+
+def test_batched_equals_staged_single_scene_and_capacity():
+    """The batched launch (warp items) against the single-scene path, which
+    takes the staged kernel (1024-column CTA items, float rows written by bulk
+    copies) for scenes on the 16-byte grid with a float output and at most 6
+    bands: the two different kernels agree bit for bit, on scenes of 1-8
+    bands, W = 0 and 2 mod 4, several 1024-column strips and ragged ones, a
+    uint8-only output, and a full table of 8-band scenes."""
+    mix = [scenegen.SceneSpec(64, 1028, 8, O.D4, 1), scenegen.SceneSpec(66, 2052, 3, O.HAAR, 2),
+           scenegen.SceneSpec(34, 1030, 7, O.D4, 3), scenegen.SceneSpec(8, 4, 1, O.D4, 4),
+           scenegen.SceneSpec(130, 516, 6, O.D4, 5), scenegen.SceneSpec(12, 3000, 2, O.HAAR, 6)]
+    full = [scenegen.SceneSpec(6 + 2 * (i % 4), 8 + 4 * (i % 9), 8, O.D4 if i % 3 else O.HAAR, 200 + i)
+            for i in range(_C.MAX_SCENES)]
+    assert all(sp.W % 4 == 0 for sp in full)
+    for specs in (mix, full):
+        scenes, keep = _make(specs)
+        if specs is mix:  # a uint8-only scene
+            sp, pan, ms, out, out8 = keep[1]
+            scenes[1] = _C.make_scene(pan, ms, sp.wavelet, None, out8)
+        ws = _workspace()
+        _C.dwtfuse_fuse_batched(scenes, ws)
+        torch.cuda.synchronize()
+        assert _C.dwtfuse_get_last_device_status(ws) == _C.OK
+        for i, (sp, pan, ms, out, out8) in enumerate(keep):
+            f, u = fuse(pan, ms, sp.wavelet, f32=True, u8=True)
+            torch.cuda.synchronize()
+            if not (specs is mix and i == 1):
+                assert torch.equal(out, f), sp
+            assert torch.equal(out8, u), sp
