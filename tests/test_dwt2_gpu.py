@@ -106,3 +106,79 @@ def test_dwt2_full_size_sampled_and_round_trip():
     _C.dwtfuse_idwt2(Z, 1, None, back)
     torch.cuda.synchronize()
     assert torch.equal(back, img)
+
+
+# Widths the staged forward takes for D4 (W % 8 == 0, a 16-byte-aligned
+# coefficient plane and a last 1024-column strip at least 7/8 full; Haar runs
+# warp items there):
+# one and several strips, a ragged last strip, odd H/2, both step parities.
+STAGED = [(34, 1024), (66, 2048), (130, 1976), (20, 3064), (6, 4096)]
+
+
+@pytest.mark.parametrize("wav", [0, 1])
+@pytest.mark.parametrize("shape", STAGED)
+def test_staged_transforms_match_oracle(wav, shape):
+    """The staged forward (uint8 and float images) against the oracle, the
+    inverse at the same widths (float and uint8 outputs), and the round
+    trip."""
+    rng = np.random.default_rng(sum(shape) + wav)
+    img = rng.integers(0, 256, shape).astype(np.uint8)
+    x = torch.from_numpy(img).to(DEV)
+    Z = torch.empty(shape, device=DEV)
+    Zf = torch.empty(shape, device=DEV)
+    _C.dwtfuse_dwt2(x, wav, Z)
+    _C.dwtfuse_dwt2(x.float(), wav, Zf)
+    torch.cuda.synchronize()
+    ref = O.dwt2(img.astype(np.float64), wav)
+    for got in (Z, Zf):
+        g = got.cpu().numpy()
+        if wav == 0:
+            np.testing.assert_array_equal(g, ref.astype(np.float32))
+        else:
+            assert np.abs(g - ref).max() <= 5e-4
+    C = O.dwt2(img.astype(np.float64), wav) + rng.normal(0, 8, shape)
+    if wav == 0:
+        C = np.round(C * 4) / 4
+    C32 = torch.from_numpy(C.astype(np.float32)).to(DEV)
+    f = torch.empty(shape, device=DEV)
+    u = torch.empty(shape, dtype=torch.uint8, device=DEV)
+    _C.dwtfuse_idwt2(C32, wav, f, u)
+    torch.cuda.synchronize()
+    iref = O.idwt2(C.astype(np.float32).astype(np.float64), wav)
+    if wav == 0:
+        np.testing.assert_array_equal(f.cpu().numpy().astype(np.float64), iref)
+        np.testing.assert_array_equal(u.cpu().numpy(), O.to_u8(iref))
+    else:
+        assert np.abs(f.cpu().numpy() - iref).max() <= 5e-4
+        du = np.abs(u.cpu().numpy().astype(int) - O.to_u8(iref).astype(int))
+        assert du.max() <= 1
+    back = torch.empty(shape, dtype=torch.uint8, device=DEV)
+    backf = torch.empty(shape, device=DEV)
+    _C.dwtfuse_idwt2(Z, wav, backf, back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, x)
+
+
+def test_staged_transform_kernels_are_launched():
+    """Kernel names seen by the profiler: a 2048-wide image runs the staged
+    forward, a 1030-wide one the warp-item forward; the inverse runs warp
+    items at both widths."""
+    prof = pytest.importorskip("torch.profiler")
+    with prof.profile(activities=[prof.ProfilerActivity.CUDA]):  # the first session can miss kernels
+        torch.zeros(1, device=DEV).add_(1)
+        torch.cuda.synchronize()
+    names = {}
+    for W in (2048, 1030):
+        x = torch.zeros((8, W), dtype=torch.uint8, device=DEV)
+        Z = torch.empty((8, W), device=DEV)
+        out = torch.empty((8, W), device=DEV)
+        torch.cuda.synchronize()
+        with prof.profile(activities=[prof.ProfilerActivity.CUDA]) as pr:
+            _C.dwtfuse_dwt2(x, 1, Z)
+            _C.dwtfuse_idwt2(Z, 1, out)
+            torch.cuda.synchronize()
+        names[W] = {e.name for e in pr.events() if "dwt2" in e.name}
+    if not names[2048] and not names[1030]:
+        pytest.skip("profiler recorded no kernels")
+    assert sum("dwt2_staged_kernel" in n for n in names[2048]) == 1, names
+    assert not any("dwt2_staged_kernel" in n for n in names[1030]), names
