@@ -108,7 +108,9 @@ def test_band_chunk_knobs_keep_results(f, g):
 
     import scenegen
     from paper_1803_00737_gb300 import _C
-    for wav, (H, W), B in [(1, (64, 136), 8), (0, (66, 258), 7), (1, (130, 250), 6)]:
+    # (the 2048-wide scenes run the staged single-scene kernel, chunked by the knob)
+    for wav, (H, W), B in [(1, (64, 136), 8), (0, (66, 258), 7), (1, (130, 250), 6), (1, (34, 2048), 6),
+                           (0, (20, 2048), 5)]:
         pan, ms = scenegen.make_scene(H, W, B, seed=H)
         pan, ms = pan.cuda(), ms.cuda()
         ref = torch.empty((B, H, W), device="cuda")
