@@ -751,6 +751,8 @@ def run_case(args) -> None:
     if args.rows or args.fwd_chunk or args.bwd_chunk:  # launch-shape knobs for this case
         from paper_1803_00737_gb300 import tune
         tune.apply(tune.LaunchShape(args.rows, 0, args.fwd_chunk, args.bwd_chunk))
+    if args.no_staging:  # the warp-strip forward instead of the staged one
+        _C.dwtfuse_set_fuse_staging(False)
     pan, ms = scenegen.make_scene(H, W, B, seed=0, blob_scale=BLOB_SCALE, device=dev)
     extra = {}
     if args.case == "metrics":
@@ -812,7 +814,7 @@ def run_case(args) -> None:
     torch.cuda.synchronize()
     ms_call = e0.elapsed_time(e1) / max(1, args.steps)
     print(json.dumps({"case": args.case, "H": H, "W": W, "bands": B, "calls": args.steps, "ms": ms_call,
-                      "knobs": {"rows": args.rows, "fwd_chunk": args.fwd_chunk, "bwd_chunk": args.bwd_chunk},
+                      "knobs": {"rows": args.rows, "fwd_chunk": args.fwd_chunk, "bwd_chunk": args.bwd_chunk, "staging": not args.no_staging},
                       "algorithmic_GBps": nbytes / (ms_call / 1e3) / 1e9, **extra}))
 
 
@@ -841,6 +843,8 @@ def main() -> None:
     ap.add_argument("--rows", type=int, default=0, help="rows-per-item knob of a --case run (0: default)")
     ap.add_argument("--fwd-chunk", type=int, default=0, help="forward band-chunk knob of a --case run")
     ap.add_argument("--bwd-chunk", type=int, default=0, help="adjoint band-chunk knob of a --case run")
+    ap.add_argument("--no-staging", action="store_true",
+                    help="a --case run on the warp-strip forward kernel (dwtfuse_set_fuse_staging(0))")
     args = ap.parse_args()
     if args.case:
         run_case(args)

@@ -357,6 +357,18 @@ int dwtfuse_set_rows_per_item(int rows);
 int dwtfuse_set_band_chunks(int fwd, int bwd);
 
 /*
+ * Store-path knob of the single-scene forward (a launch-shape choice, no
+ * counterpart in the paper): with on = 1 (the default) dwtfuse_fuse takes the
+ * staged kernel where it applies (rows on the 16-byte grid, a float output, at
+ * most 6 bands per launch, whole 1024-column CTA strips, the last one at least
+ * 7/8 full), which writes the float rows through shared memory and bulk
+ * copies; with on = 0 it runs the warp-strip kernels everywhere.  The outputs
+ * are the same bits either way.  Process-wide; other values are
+ * DWTFUSE_EINVAL.
+ */
+int dwtfuse_set_fuse_staging(int on);
+
+/*
  * Test hook for the metric passes' bounded waits (no counterpart in the
  * paper).  With on = 1, every later metrics call whose PAN-resolution pass
  * stages unaligned rows (W % 16 != 0, uint8 data) makes one warp post 16 bytes

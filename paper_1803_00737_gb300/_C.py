@@ -83,6 +83,7 @@ _SIGS = {
     "dwtfuse_get_last_device_status": (_i, [_vp, _vp]),
     "dwtfuse_set_rows_per_item": (_i, [_i]),
     "dwtfuse_set_band_chunks": (_i, [_i, _i]),
+    "dwtfuse_set_fuse_staging": (_i, [_i]),
     "dwtfuse_set_metric_wait_test": (_i, [_i]),
     "dwtfuse_fuse_batched_noalloc": (_i, [ctypes.POINTER(Scene), _i, _i, _i, _vp]),
     "dwtfuse_metrics_workspace_size": (_sz, []),
@@ -482,6 +483,11 @@ def dwtfuse_set_rows_per_item(rows: int) -> None:
 def dwtfuse_set_band_chunks(fwd: int, bwd: int) -> None:
     """Most bands per forward / adjoint launch (0 = library default; see dwtfuse.h)."""
     _check(lib().dwtfuse_set_band_chunks(int(fwd), int(bwd)), "dwtfuse_set_band_chunks")
+
+
+def dwtfuse_set_fuse_staging(on: bool) -> None:
+    """Let the single-scene forward take the staged kernel where it applies (default on; see dwtfuse.h)."""
+    _check(lib().dwtfuse_set_fuse_staging(int(bool(on))), "dwtfuse_set_fuse_staging")
 
 
 def dwtfuse_set_metric_wait_test(on: bool) -> None:

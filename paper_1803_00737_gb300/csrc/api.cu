@@ -21,6 +21,7 @@ std::atomic<int> g_rows{0};  // 0: balanced_rows() per launch
 std::atomic<int> g_fwd_chunk{0};  // dwtfuse_set_band_chunks (0: library default)
 std::atomic<int> g_bwd_chunk{0};
 std::atomic<int> g_metric_wait_test{0};  // dwtfuse_set_metric_wait_test
+std::atomic<int> g_staging{1};           // dwtfuse_set_fuse_staging
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 }  // namespace
 
@@ -92,6 +93,7 @@ cudaError_t sm_count(int *out) {
 int rows_per_item() { return g_rows.load(std::memory_order_relaxed); }
 int fwd_band_chunk() { return g_fwd_chunk.load(std::memory_order_relaxed); }
 int bwd_band_chunk() { return g_bwd_chunk.load(std::memory_order_relaxed); }
+int fuse_staging() { return g_staging.load(std::memory_order_relaxed); }
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DWTFUSE_OK;
@@ -244,6 +246,12 @@ int dwtfuse_set_band_chunks(int fwd, int bwd) {
     if (fwd < 0 || fwd > kChunkBands || bwd < 0 || bwd > kChunkBands) return DWTFUSE_EINVAL;
     g_fwd_chunk.store(fwd, std::memory_order_relaxed);
     g_bwd_chunk.store(bwd, std::memory_order_relaxed);
+    return DWTFUSE_OK;
+}
+
+int dwtfuse_set_fuse_staging(int on) {
+    if (on != 0 && on != 1) return DWTFUSE_EINVAL;
+    g_staging.store(on, std::memory_order_relaxed);
     return DWTFUSE_OK;
 }
 

@@ -115,7 +115,7 @@ void *fwd_kernel_ptr(bool f32, int wav, int nb, bool alt) {
 cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream_t stream) {
     // Large scenes whose rows lie on the 16-byte grid with a float output: the
     // staged kernel (its float rows go out as bulk copies).
-    if (fuse_staged_applies(s)) return launch_fuse_staged(s, R, stream);
+    if (fuse_staging() && fuse_staged_applies(s)) return launch_fuse_staged(s, R, stream);
     // Bands go in chunks of up to 8; the shifted-row instance (W % 4 == 2)
     // holds more live registers per band and takes balanced chunks of <= 6;
     // a band-chunk knob (autotuner) caps both, in balanced chunks.

@@ -98,6 +98,9 @@ struct DwtLaunch {
 int rows_per_item();
 int fwd_band_chunk();
 int bwd_band_chunk();
+// dwtfuse_set_fuse_staging: 1 (default) lets the single-scene forward take the
+// staged kernel where it applies, 0 keeps the warp-item kernels.
+int fuse_staging();
 
 // Resident CTAs per SM for a kernel at a block size (cached per kernel).
 cudaError_t resident_blocks(const void *fn, int threads, int *out);

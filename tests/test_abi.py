@@ -157,6 +157,13 @@ def test_rows_knob(L):
     assert L.dwtfuse_set_rows_per_item(0) == _C.OK
 
 
+def test_staging_knob(L):
+    assert L.dwtfuse_set_fuse_staging(2) == _C.EINVAL
+    assert L.dwtfuse_set_fuse_staging(-1) == _C.EINVAL
+    assert L.dwtfuse_set_fuse_staging(0) == _C.OK
+    assert L.dwtfuse_set_fuse_staging(1) == _C.OK
+
+
 def test_cpu_tensors_are_rejected():
     torch = pytest.importorskip("torch")
     pan = torch.zeros((4, 4), dtype=torch.uint8)

@@ -150,3 +150,22 @@ def test_shifted_row_instance_is_launched():
         pytest.skip("profiler recorded no kernels")
     assert any("fuse_staged_kernel" in n for n in names[1024]), names
     assert any("fuse_fwd_kernel" in n and "true>" in n for n in names[1030]), names
+
+
+@pytest.mark.parametrize("wav", [O.HAAR, O.D4])
+@pytest.mark.parametrize("shape,B", [((64, 1024), 6), ((34, 2048), 4), ((66, 1920), 3), ((40, 4092), 5)])
+def test_staging_knob_gives_the_same_bits(wav, shape, B):
+    """dwtfuse_set_fuse_staging(0) runs the warp-strip kernel on scenes the
+    staged kernel takes; the outputs are the same bits, and the staged run
+    matches the oracle."""
+    pan, ms = rand_scene(*shape, B, seed=sum(shape) + B)
+    try:
+        a, ua, ok_a = run(pan, ms, wav)
+        _C.dwtfuse_set_fuse_staging(False)
+        b, ub, ok_b = run(pan, ms, wav)
+    finally:
+        _C.dwtfuse_set_fuse_staging(True)
+    assert ok_a and ok_b
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ua, ub)
+    check(pan, ms, wav, a, ua)
