@@ -76,8 +76,11 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # after the scoring emitter took 7-8 bands (the 6-band body unchanged):
     # read 689,794,219 + write 7,989,526,784 (mean of 3 launches)
     "af32194f41e5": 8679321003.0,
+    # the window sums in TMEM (16-warp CTAs), items round the CTAs first:
+    # read 689,499,904 + write 7,989,635,328 (mean of 3 launches)
+    "6b8106a5e69f": 8679135232.0,
 }
-KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh")
+KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh", "tmem.cuh")
 
 
 def kernel_hash() -> str:
