@@ -79,6 +79,9 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # the window sums in TMEM (16-warp CTAs), items round the CTAs first:
     # read 689,499,904 + write 7,989,635,328 (mean of 3 launches)
     "6b8106a5e69f": 8679135232.0,
+    # the same 6-band body after 7 bands joined the TMEM kernel:
+    # read 689,457,322 + write 7,989,600,853 (mean of 3 launches)
+    "9f3157beffa0": 8679058175.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh", "tmem.cuh")
 

@@ -22,14 +22,16 @@
 // kernel of metrics.cu complete the figures unchanged.
 //
 // Where the running sums live:
-//  * up to 6 bands (fuse_metrics_kernel): in the lane's own cells of tensor
+//  * up to 7 bands (fuse_metrics_kernel): in the lane's own cells of tensor
 //    memory (TMEM, tcgen05.ld / tcgen05.st), read, added to and written back
-//    every 4 MS rows without shared-memory traffic; the freed shared memory
-//    parks 4 MS rows.  A CTA that holds TMEM runs alone on its SM, so a CTA is
-//    16 warps (the SM's 64 K registers at 128 per thread).  16384^2 x 6:
-//    1.525 -> 1.493 ms against the shared-memory form below.
-//  * 7-8 bands (fuse_metrics_wide_kernel): in per-lane shared-memory slots,
-//    8-warp CTAs, two per SM; the TMEM form spills there and ran 7 % slower.
+//    every SR MS rows without shared-memory traffic; the freed shared memory
+//    parks 4 MS rows (7 bands: 2).  A CTA that holds TMEM runs alone on its
+//    SM, so a CTA is 16 warps (the SM's 64 K registers at 128 per thread).
+//    Against the shared-memory form below: 16384^2 x 6 1.525 -> 1.493 ms,
+//    16384^2 x 7 2.212 -> 2.057 ms.
+//  * 8 bands (fuse_metrics_wide_kernel): in per-lane shared-memory slots,
+//    8-warp CTAs, two per SM; the TMEM form spills there and ran 7-15 %
+//    slower.
 #include "fuse_tile.cuh"
 #include "launch.h"
 #include "metric_q.cuh"
@@ -123,7 +125,9 @@ struct FmLayout {  // TMEM form, up to 6 bands
     static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs (b < c), then band-PAN pairs
     static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
     static constexpr int NT = NS + NB;                // TMEM cells per lane: window sums, squared errors
-    static constexpr int SR = 4;  // MS rows parked before they are scored (divides 16)
+    // MS rows parked before they are scored (divides 16): 4 rows of 6 bands
+    // take 12.4 KB of shared memory per warp, 7 bands park 2.
+    static constexpr int SR = NB <= 6 ? 4 : 2;
     // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
     static constexpr int kTile = K * 2 * SR * 32;     // uint8 words of 2 SR PAN rows: bands, PAN
     static constexpr int kRep = NB * SR * 32;         // MS reference words of SR MS rows
@@ -268,7 +272,14 @@ struct MetricEmit {
         const int64_t y_win = ((2 * m) / 32) * 32;
         const bool row_full = y_win + 32 <= s.H;
         const bool win_in = row_full && x0 + 32 * ((lane >> 3) + 1) <= s.W;
-        score_cells<0, NS, true>(2 * (r + 1), fl, win_in);
+        if constexpr (NB <= 6) {
+            score_cells<0, NS, true>(2 * (r + 1), fl, win_in);
+        } else {  // 7 bands: three passes over the parked words, fewer cells live at once
+            constexpr int A = 2 * K, B = 2 * K + P / 2;
+            score_cells<0, A, true>(2 * (r + 1), fl, win_in);
+            score_cells<A, B, false>(2 * (r + 1), fl, win_in);
+            score_cells<B, NS, false>(2 * (r + 1), fl, win_in);
+        }
         fresh = fl;
         if (fl) finish_window(row_full);
     }
@@ -626,7 +637,7 @@ struct FmKernel {
 
 template <int WAV, int NB>
 FmKernel fm_of() {
-    if constexpr (NB <= 6)
+    if constexpr (NB <= 7)
         return {reinterpret_cast<void *>(&fuse_metrics_kernel<uint8_t, WAV, NB>), kFmTmThreads, FmLayout<NB>::kSmem,
                 FmLayout<NB>::kTmemCols};
     else
