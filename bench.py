@@ -82,6 +82,9 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # the same 6-band body after 7 bands joined the TMEM kernel:
     # read 689,457,322 + write 7,989,600,853 (mean of 3 launches)
     "9f3157beffa0": 8679058175.0,
+    # the same 6-band body after 8 bands joined the TMEM kernel (12-warp CTAs):
+    # read 689,428,992 + write 7,989,767,594 (mean of 3 launches)
+    "117fcefd467f": 8679196586.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh", "tmem.cuh")
 

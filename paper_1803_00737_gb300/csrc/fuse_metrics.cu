@@ -8,30 +8,30 @@
 //
 // Work item: a warp strip of 128 PAN columns (four windows side by side, 8
 // lanes each) over R MS rows, R a multiple of 16 and items starting on window
-// rows.  Every SR MS rows the warp parks its uint8 pixels, the matching PAN
-// pixels and the MS reference values in a per-warp shared tile (a private
-// spill area: each lane reads back only its own words, so the fusion's
-// registers are free again) and adds their terms to its running sums over
-// the current window row (S1, S2 of every image, S_xy of every pair, squared
-// errors): signed-byte dp4a sums, exact in int32.  At the end of a window row
-// the 8 lanes of each window add up their sums, lane j of the window computes
-// Q for pairs j, j + 8, ... (integer numerators, FP32 ratio), and the value
-// goes to a per-warp float slot of that window position; squared errors go to
-// per-lane int64 slots.  The CTA writes one partial row in the layout of the
-// separate PAN-resolution pass, so the MS-resolution pass and the finalize
-// kernel of metrics.cu complete the figures unchanged.
+// rows.  Every SR MS rows (4 for up to 6 bands, else 2) the warp parks its
+// uint8 pixels, the matching PAN pixels and the MS reference values in a
+// per-warp shared tile (a private spill area: each lane reads back only its
+// own words, so the fusion's registers are free again) and adds their terms
+// to its running sums over the current window row (S1, S2 of every image,
+// S_xy of every pair, squared errors: signed-byte dp4a sums, exact in int32).
+// The running sums live in the lane's own cells of tensor memory (TMEM,
+// tcgen05.ld / tcgen05.st): read, added to and written back without
+// shared-memory traffic (7-8 bands in two or three passes over the parked
+// words, fewer cells live at once).  At the end of a window row the 8 lanes of
+// each window add their sums into the window's shared-memory sums, lane j of
+// the window computes Q for pairs j, j + 8, ... (integer numerators, FP32
+// ratio), and the value goes to a per-warp float slot of that window
+// position; squared errors go to per-lane int64 slots.  The CTA writes one
+// partial row in the layout of the separate PAN-resolution pass, so the
+// MS-resolution pass and the finalize kernel of metrics.cu complete the
+// figures unchanged.
 //
-// Where the running sums live:
-//  * up to 7 bands (fuse_metrics_kernel): in the lane's own cells of tensor
-//    memory (TMEM, tcgen05.ld / tcgen05.st), read, added to and written back
-//    every SR MS rows without shared-memory traffic; the freed shared memory
-//    parks 4 MS rows (7 bands: 2).  A CTA that holds TMEM runs alone on its
-//    SM, so a CTA is 16 warps (the SM's 64 K registers at 128 per thread).
-//    Against the shared-memory form below: 16384^2 x 6 1.525 -> 1.493 ms,
-//    16384^2 x 7 2.212 -> 2.057 ms.
-//  * 8 bands (fuse_metrics_wide_kernel): in per-lane shared-memory slots,
-//    8-warp CTAs, two per SM; the TMEM form spills there and ran 7-15 %
-//    slower.
+// A CTA that holds TMEM runs alone on its SM: up to 7 bands a CTA is 16 warps
+// (the SM's 64 K registers at 128 per thread), 8 bands 12 warps at up to 168
+// registers (at 128 the 8-band walker spills).  Against per-lane
+// shared-memory slots for the sums (8-warp CTAs, two per SM): 16384^2 x 6
+// 1.525 -> 1.493 ms, 16384^2 x 7 2.212 -> 2.057 ms, 16382^2 x 8 2.805 ->
+// 2.554 ms.
 #include "fuse_tile.cuh"
 #include "launch.h"
 #include "metric_q.cuh"
@@ -114,13 +114,9 @@ __device__ __forceinline__ void metric_pan(uint32_t *tile, int lane, int r, cons
     tile[(NB * 2 * SR + 2 * r + 1) * 32 + lane] = pack4(f2u8(pan1[0]), f2u8(pan1[1]), f2u8(pan1[2]), f2u8(pan1[3]));
 }
 
-// ---------------------------------------------------------------- up to 6 bands: sums in TMEM
-
-constexpr int kFmTmThreads = 512;
-constexpr int kFmTmWarps = kFmTmThreads / 32;
 
 template <int NB>
-struct FmLayout {  // TMEM form, up to 6 bands
+struct FmLayout {
     static constexpr int K = NB + 1;                  // images: NB bands, then PAN
     static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs (b < c), then band-PAN pairs
     static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
@@ -128,6 +124,8 @@ struct FmLayout {  // TMEM form, up to 6 bands
     // MS rows parked before they are scored (divides 16): 4 rows of 6 bands
     // take 12.4 KB of shared memory per warp, 7 bands park 2.
     static constexpr int SR = NB <= 6 ? 4 : 2;
+    static constexpr int kThreads = NB <= 7 ? 512 : 384;
+    static constexpr int kWarps = kThreads / 32;
     // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
     static constexpr int kTile = K * 2 * SR * 32;     // uint8 words of 2 SR PAN rows: bands, PAN
     static constexpr int kRep = NB * SR * 32;         // MS reference words of SR MS rows
@@ -135,10 +133,10 @@ struct FmLayout {  // TMEM form, up to 6 bands
     static constexpr int kQ = 4 * P;                  // float Q sums per window position
     static constexpr int kWords = (kTile + kRep + kGsum + kQ + 1) & ~1;
     static constexpr int kWarpBytes = kWords * 4 + NB * 32 * 8;  // + int64 squared errors per lane
-    static constexpr int kSmem = kFmTmWarps * kWarpBytes + 16;     // + the TMEM base address
+    static constexpr int kSmem = kWarps * kWarpBytes + 16;     // + the TMEM base address
     // TMEM: warps w, w + 4, w + 8, w + 12 share a quarter of the lanes, side by side.
     static constexpr int kWarpTmem = fm_pow2_at_least(NT, 16);
-    static constexpr int kTmemCols = fm_pow2_at_least(kFmTmWarps / 4 * kWarpTmem, 32);
+    static constexpr int kTmemCols = fm_pow2_at_least((kWarps + 3) / 4 * kWarpTmem, 32);
     static_assert(NT <= 64 && kTmemCols <= 512, "TMEM columns of an SM");
 };
 
@@ -274,10 +272,14 @@ struct MetricEmit {
         const bool win_in = row_full && x0 + 32 * ((lane >> 3) + 1) <= s.W;
         if constexpr (NB <= 6) {
             score_cells<0, NS, true>(2 * (r + 1), fl, win_in);
-        } else {  // 7 bands: three passes over the parked words, fewer cells live at once
+        } else if constexpr (NB == 7) {  // 7 bands: three passes over the parked words, fewer cells live at once
             constexpr int A = 2 * K, B = 2 * K + P / 2;
             score_cells<0, A, true>(2 * (r + 1), fl, win_in);
             score_cells<A, B, false>(2 * (r + 1), fl, win_in);
+            score_cells<B, NS, false>(2 * (r + 1), fl, win_in);
+        } else {
+            constexpr int B = 2 * K + P / 2;
+            score_cells<0, B, true>(2 * (r + 1), fl, win_in);
             score_cells<B, NS, false>(2 * (r + 1), fl, win_in);
         }
         fresh = fl;
@@ -286,7 +288,7 @@ struct MetricEmit {
 };
 
 template <typename T, int WAV, int NB>
-__global__ void __launch_bounds__(kFmTmThreads, 1)
+__global__ void __launch_bounds__(FmLayout<NB>::kThreads, 1)
 fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int stride, int *ctas_out,
                     int64_t strips_x, int64_t items, int R) {
     using L = FmLayout<NB>;
@@ -298,7 +300,7 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
     int *gsum = reinterpret_cast<int *>(rep + L::kRep);
     float *qs = reinterpret_cast<float *>(gsum + L::kGsum);
     long long *se64 = reinterpret_cast<long long *>(wb + L::kWords * 4);
-    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(fm_smem + kFmTmWarps * L::kWarpBytes);
+    uint32_t *tmem_base = reinterpret_cast<uint32_t *>(fm_smem + L::kWarps * L::kWarpBytes);
     // Let a programmatic dependent (the MS-resolution pass) be scheduled as
     // this grid drains (no-op without one).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -315,7 +317,7 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
 
     // Items go round the CTAs first (warp w of CTA b starts at item w G + b,
     // G CTAs), so a scene with fewer items than warps still spreads over every SM.
-    const int64_t nwarps = (int64_t)gridDim.x * kFmTmWarps;
+    const int64_t nwarps = (int64_t)gridDim.x * L::kWarps;
     for (int64_t it = (int64_t)warp * gridDim.x + blockIdx.x; it < items; it += nwarps) {
         const int64_t sx = it % strips_x, sy = it / strips_x;
         const int64_t x0 = sx * kWarpCols;
@@ -340,282 +342,12 @@ fuse_metrics_kernel(const __grid_constant__ SceneArgs s, double *partial, int st
     // One partial row per CTA, in the layout of the PAN-resolution pass:
     // Q sums of the P pairs, then the NB squared-error sums (fixed order).
     double *outp = partial + (int64_t)blockIdx.x * stride;
-    for (int k = threadIdx.x; k < L::P + NB; k += kFmTmThreads) {
+    for (int k = threadIdx.x; k < L::P + NB; k += L::kThreads) {
         double acc = 0.0;
-        for (int w = 0; w < kFmTmWarps; ++w) {
+        for (int w = 0; w < L::kWarps; ++w) {
             const unsigned char *wbw = fm_smem + w * L::kWarpBytes;
             if (k < L::P) {
                 const float *qw = reinterpret_cast<const float *>(wbw) + L::kTile + L::kRep + L::kGsum;
-                for (int g = 0; g < 4; ++g) acc += (double)qw[g * L::P + k];
-            } else {
-                const long long *sw = reinterpret_cast<const long long *>(wbw + L::kWords * 4);
-                long long t = 0;
-                for (int l = 0; l < 32; ++l) t += sw[(k - L::P) * 32 + l];
-                acc += (double)t;
-            }
-        }
-        outp[k] = acc;
-    }
-}
-
-// ---------------------------------------------------------------- 7-8 bands: sums in shared memory
-
-constexpr int kFmWideThreads = 256;
-constexpr int kFmWideWarps = kFmWideThreads / 32;
-
-template <int NB>
-struct FmWideLayout {  // shared-memory form, 7-8 bands
-    static constexpr int K = NB + 1;                  // images: NB bands, then PAN
-    static constexpr int P = NB * (NB - 1) / 2 + NB;  // band-band pairs (b < c), then band-PAN pairs
-    static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
-    // MS rows parked before they are scored: 2, or 1 for 8 bands, so that two
-    // CTAs still fit an SM's shared memory.
-    static constexpr int SR = NB <= 7 ? 2 : 1;
-    // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
-    static constexpr int kTile = K * 2 * SR * 32;     // uint8 words of 2 SR PAN rows: bands, PAN
-    static constexpr int kRep = NB * SR * 32;         // MS reference words of SR MS rows
-    static constexpr int kSums = NS * 32;
-    static constexpr int kQ = 4 * P;                  // float Q sums per window position
-    static constexpr int kWords = (kTile + kRep + kSums + kQ + 1) & ~1;
-    static constexpr int kWarpBytes = kWords * 4 + NB * 32 * 8;  // + int64 squared errors per lane
-    static constexpr int kSmem = kFmWideWarps * kWarpBytes;
-};
-
-template <int NB>
-struct MetricEmitWide {
-    using L = FmWideLayout<NB>;
-    static constexpr bool kAllLanes = true;
-    static constexpr int K = L::K, P = L::P, NS = L::NS, SR = L::SR;
-    const SceneArgs &s;
-    const LaneCols &c;
-    uint32_t *tile, *rep;
-    int *sums;
-    float *qs;
-    long long *se64;
-    int64_t x0, m_s, m_e;
-    int lane;
-    bool a4;
-    bool alt;       // W % 4 == 2 with vector-aligned planes: even rows vectorised, odd rows shifted
-    uint32_t keep;  // bytes of this lane's 4-pixel words inside the image
-
-    __device__ __forceinline__ void band(int b, int64_t m, const float *v0, const float *v1, float mn,
-                                         float mn1) const {
-        metric_band<NB, SR>(s, c, tile, rep, lane, (int)((m - m_s) & (SR - 1)), a4, alt, b, m, v0, v1, mn, mn1);
-    }
-
-    // Pair sums [LO, HI) of the tile's first `nr` PAN rows into this lane's
-    // slots (7-8 bands: the 28-36 pair sums are formed in two passes over the
-    // parked words, so that fewer of them are live next to the walker's state).
-    template <int LO, int HI>
-    __device__ __forceinline__ void pair_sums(int nr) const {
-        int sxy[HI - LO];
-#pragma unroll
-        for (int k = 0; k < HI - LO; ++k) sxy[k] = 0;
-        for (int r = 0; r < nr; ++r) {
-            int v[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = (int)(tile[(k * 2 * SR + r) * 32 + lane] ^ 0x80808080u);
-#pragma unroll
-            for (int b = 0; b < NB; ++b)
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2) {
-                    const int q = pair_index(NB, b, c2);
-                    if (c2 > b && q >= LO && q < HI) sxy[q - LO] = __dp4a(v[b], v[c2], sxy[q - LO]);
-                }
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const int q = NB * (NB - 1) / 2 + b;
-                if (q >= LO && q < HI) sxy[q - LO] = __dp4a(v[b], v[NB], sxy[q - LO]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < HI - LO; ++k) sums[(2 * K + LO + k) * 32 + lane] += sxy[k];
-    }
-
-    // Sums of the tile's first `nr` PAN rows into this lane's slots.  qon: the
-    // lane's window is inside the image (window sums wanted).
-    __device__ __forceinline__ void score(int nr, bool qon) const {
-        if constexpr (NB >= 7) {
-            int s1[K], s2[K], se[NB];
-#pragma unroll
-            for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) se[b] = 0;
-            for (int r = 0; r < nr; ++r) {
-                uint32_t f[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) f[k] = tile[(k * 2 * SR + r) * 32 + lane];
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    const uint32_t d = __vabsdiffu4(f[b], rep[(b * SR + (r >> 1)) * 32 + lane]) & keep;
-                    se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
-                }
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const int v = (int)(f[k] ^ 0x80808080u);
-                    s1[k] = __dp4a(v, 0x01010101, s1[k]);
-                    s2[k] = __dp4a(v, v, s2[k]);
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < NB; ++b) se64[b * 32 + lane] += se[b];
-            if (qon) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    sums[k * 32 + lane] += s1[k];
-                    sums[(K + k) * 32 + lane] += s2[k];
-                }
-                pair_sums<0, P / 2>(nr);
-                pair_sums<P / 2, P>(nr);
-            }
-            return;
-        }
-        int s1[K], s2[K], sxy[P], se[NB];
-#pragma unroll
-        for (int k = 0; k < K; ++k) s1[k] = s2[k] = 0;
-#pragma unroll
-        for (int k = 0; k < P; ++k) sxy[k] = 0;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) se[b] = 0;
-        for (int r = 0; r < nr; ++r) {
-            uint32_t f[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) f[k] = tile[(k * 2 * SR + r) * 32 + lane];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const uint32_t d = __vabsdiffu4(f[b], rep[(b * SR + (r >> 1)) * 32 + lane]) & keep;
-                se[b] = (int)__dp4a(d, d, (unsigned)se[b]);
-            }
-            if (qon) {
-                int v[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    v[k] = (int)(f[k] ^ 0x80808080u);  // signed bytes X - 128
-                    s1[k] = __dp4a(v[k], 0x01010101, s1[k]);
-                    s2[k] = __dp4a(v[k], v[k], s2[k]);
-                }
-                int idx = 0;
-#pragma unroll
-                for (int b = 0; b < NB; ++b)
-#pragma unroll
-                    for (int c2 = b + 1; c2 < NB; ++c2, ++idx) sxy[idx] = __dp4a(v[b], v[c2], sxy[idx]);
-#pragma unroll
-                for (int b = 0; b < NB; ++b, ++idx) sxy[idx] = __dp4a(v[b], v[NB], sxy[idx]);
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < NB; ++b) se64[b * 32 + lane] += se[b];
-        if (qon) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                sums[k * 32 + lane] += s1[k];
-                sums[(K + k) * 32 + lane] += s2[k];
-            }
-#pragma unroll
-            for (int k = 0; k < P; ++k) sums[(2 * K + k) * 32 + lane] += sxy[k];
-        }
-    }
-
-    // End of a window row: the 8 lanes of each window add up their slots
-    // (slot of the group's first lane), then lane j of the group computes Q
-    // for pairs j, j+8, ...  `full` (warp-uniform): the window row lies inside
-    // the image.  Every lane's slots are cleared.
-    __device__ __forceinline__ void flush(bool full) const {
-        const int g = lane >> 3, j = lane & 7, g0 = 8 * g;
-        if (full) {
-            __syncwarp();
-            for (int k = j; k < NS; k += 8) {
-                int t = 0;
-#pragma unroll
-                for (int l = 0; l < 8; ++l) t += sums[k * 32 + g0 + l];
-                sums[k * 32 + g0] = t;
-            }
-            __syncwarp();
-            if (x0 + 32 * (g + 1) <= s.W) {
-                for (int p = j; p < P; p += 8) {
-                    int b, c2;
-                    if (p < P - NB) {
-                        pair_bands<NB>(p, b, c2);
-                    } else {
-                        b = p - (P - NB);
-                        c2 = NB;
-                    }
-                    const float q = q_exact(sums[b * 32 + g0], sums[(K + b) * 32 + g0], sums[c2 * 32 + g0],
-                                            sums[(K + c2) * 32 + g0], sums[(2 * K + p) * 32 + g0], 1);
-                    qs[g * P + p] += q;
-                }
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int k = 0; k < NS; ++k) sums[k * 32 + lane] = 0;
-    }
-
-    __device__ __forceinline__ void row_end(int64_t m, const float *pan0, const float *pan1) const {
-        const int r = (int)((m - m_s) & (SR - 1));  // SR is 1 or 2
-        metric_pan<NB, SR>(tile, lane, r, pan0, pan1);
-        const bool last = m + 1 == m_e;
-        if (r != SR - 1 && !last) return;
-        // Rows 2m' .. 2m+1 of the window row starting at PAN row y_win.
-        const int64_t y_win = ((2 * m) / 32) * 32;
-        const bool row_full = y_win + 32 <= s.H;
-        const bool qon = row_full && x0 + 32 * ((lane >> 3) + 1) <= s.W;
-        score(2 * (r + 1), qon);
-        if ((m - m_s + 1) % kFmWinMs == 0 || last) flush(row_full);
-    }
-};
-
-template <typename T, int WAV, int NB>
-__global__ void __launch_bounds__(kFmWideThreads, 2)
-fuse_metrics_wide_kernel(const __grid_constant__ SceneArgs s, double *partial, int stride, int *ctas_out,
-                    int64_t strips_x, int64_t items, int R) {
-    using L = FmWideLayout<NB>;
-    extern __shared__ __align__(16) unsigned char fm_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *wb = fm_smem + warp * L::kWarpBytes;
-    uint32_t *tile = reinterpret_cast<uint32_t *>(wb);
-    uint32_t *rep = tile + L::kTile;
-    int *sums = reinterpret_cast<int *>(rep + L::kRep);
-    float *qs = reinterpret_cast<float *>(sums + L::kSums);
-    long long *se64 = reinterpret_cast<long long *>(wb + L::kWords * 4);
-    // Let a programmatic dependent (the MS-resolution pass) be scheduled as
-    // this grid drains (no-op without one).
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ctas_out = (int)gridDim.x;  // partial rows, for the finalize
-    for (int k = 0; k < L::NS; ++k) sums[k * 32 + lane] = 0;
-    for (int k = lane; k < L::kQ; k += 32) qs[k] = 0.f;
-    for (int b = 0; b < NB; ++b) se64[b * 32 + lane] = 0;
-    __syncwarp();
-
-    // Items go round the CTAs first (as in fuse_metrics_kernel).
-    const int64_t nwarps = (int64_t)gridDim.x * kFmWideWarps;
-    for (int64_t it = (int64_t)warp * gridDim.x + blockIdx.x; it < items; it += nwarps) {
-        const int64_t sx = it % strips_x, sy = it / strips_x;
-        const int64_t x0 = sx * kWarpCols;
-        const int64_t m_s = sy * R;
-        const int64_t m_e = min(m_s + (int64_t)R, s.H >> 1);
-        const LaneCols c = lane_cols(x0, lane, s.W);
-        const int64_t x = x0 + 4 * lane;
-        const uint32_t keep = x + 4 <= s.W ? 0xffffffffu : (x + 2 <= s.W ? 0x0000ffffu : 0u);
-        const bool a4 = s.a4 != 0, alt = !a4 && s.alt != 0;
-        const bool lde = a4 || (alt && c.two);  // 4-pixel PAN loads on even rows
-        MetricEmitWide<NB> out{s, c, tile, rep, sums, qs, se64, x0, m_s, m_e, lane, a4, alt, keep};
-        if (WAV == 0)
-            haar_rows<T, NB>(s, c, lde, a4, m_s, m_e, 0, NB, out);
-        else
-            d4_rows<T, NB>(s, c, lde, a4, m_s, m_e, 0, NB, out);
-    }
-
-    // One partial row per CTA, in the layout of the PAN-resolution pass:
-    // Q sums of the P pairs, then the NB squared-error sums (fixed order).
-    __syncthreads();
-    double *outp = partial + (int64_t)blockIdx.x * stride;
-    for (int k = threadIdx.x; k < L::P + NB; k += kFmWideThreads) {
-        double acc = 0.0;
-        for (int w = 0; w < kFmWideWarps; ++w) {
-            const unsigned char *wbw = fm_smem + w * L::kWarpBytes;
-            if (k < L::P) {
-                const float *qw = reinterpret_cast<const float *>(wbw) + L::kTile + L::kRep + L::kSums;
                 for (int g = 0; g < 4; ++g) acc += (double)qw[g * L::P + k];
             } else {
                 const long long *sw = reinterpret_cast<const long long *>(wbw + L::kWords * 4);
@@ -637,12 +369,8 @@ struct FmKernel {
 
 template <int WAV, int NB>
 FmKernel fm_of() {
-    if constexpr (NB <= 7)
-        return {reinterpret_cast<void *>(&fuse_metrics_kernel<uint8_t, WAV, NB>), kFmTmThreads, FmLayout<NB>::kSmem,
-                FmLayout<NB>::kTmemCols};
-    else
-        return {reinterpret_cast<void *>(&fuse_metrics_wide_kernel<uint8_t, WAV, NB>), kFmWideThreads,
-                FmWideLayout<NB>::kSmem, 0};
+    return {reinterpret_cast<void *>(&fuse_metrics_kernel<uint8_t, WAV, NB>), FmLayout<NB>::kThreads,
+            FmLayout<NB>::kSmem, FmLayout<NB>::kTmemCols};
 }
 
 FmKernel fm_kernel(int wav, int nb) {
