@@ -782,6 +782,14 @@ def run_case(args) -> None:
         ws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
         call = lambda: _C.dwtfuse_fuse_and_score(pan, ms, WAVELET, of, ou, ws)  # noqa: E731
         nbytes = H * W * (1.0 + B * (0.25 + 4.0 + 1.0))
+    elif args.case == "score_finish":  # the MS-resolution pass and the finalize of the fused form
+        of = torch.empty((B, H, W), dtype=torch.float32, device=dev)
+        ou = torch.empty((B, H, W), dtype=torch.uint8, device=dev)
+        ws = torch.empty(_C.dwtfuse_metrics_workspace_size(), dtype=torch.uint8, device=dev)
+        res = torch.zeros(4, dtype=torch.float64, device=dev)
+        _C.dwtfuse_fuse_and_score(pan, ms, WAVELET, of, ou, ws)
+        call = lambda: _C.dwtfuse_score_finish(ms, pan, ou, ws, res)  # noqa: E731
+        nbytes = H * W * (B * 0.25 + 1.0)  # MS bands and PAN read once
     elif args.case in ("dwt2", "idwt2"):
         Z = torch.empty((H, W), dtype=torch.float32, device=dev)
         _C.dwtfuse_dwt2(pan, WAVELET, Z)
@@ -845,7 +853,8 @@ def main() -> None:
                     help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--case", choices=["metrics", "fuse", "fuse_score", "backward", "dwt2", "idwt2", "rows"],
+    ap.add_argument("--case", choices=["metrics", "fuse", "fuse_score", "score_finish", "backward", "dwt2", "idwt2",
+                                       "rows"],
                     help="time one library call alone at --side x --width with --bands (profiling aid)")
     ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
     ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")
