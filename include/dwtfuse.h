@@ -215,6 +215,11 @@ int dwtfuse_qnr(const void *fused, int fused_dtype, const void *const *ms, const
  * workspace is the metrics workspace.  Asynchronous on `stream`, capturable
  * in a CUDA graph.  The ERGAS value equals the separate calls' exactly; Q
  * sums are accumulated in another order (agreement to ~1e-6).
+ * The on-chip scoring keeps each lane's running sums in tensor memory (TMEM):
+ * every CTA of that kernel allocates 64-256 of its SM's 512 TMEM columns at
+ * start and frees them at exit, and runs alone on its SM.  A kernel of another
+ * library that holds TMEM on the same SM at the same time (another stream)
+ * makes those CTAs wait for free columns until it releases them.
  */
 int dwtfuse_fuse_metrics(const void *pan, const void *const *ms, int bands, int64_t H, int64_t W,
                          int wavelet, int in_dtype, float *out_f32, uint8_t *out_u8, void *workspace,
@@ -299,7 +304,10 @@ int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, si
 
 /*
  * Reads (synchronously, on `stream`) the device status word of a batched
- * workspace: DWTFUSE_OK, or the first device-side error recorded.
+ * workspace: DWTFUSE_OK, or the first device-side error recorded.  With
+ * workspace = NULL it reads the status word of the last
+ * dwtfuse_fuse_batched_noalloc call on the current device (DWTFUSE_OK if
+ * there was none); that read allocates nothing either.
  */
 int dwtfuse_get_last_device_status(const void *workspace, void *stream);
 
@@ -328,7 +336,9 @@ int dwtfuse_get_last_device_status(const void *workspace, void *stream);
  * Every call shares the one array, which keeps the last call's contents; each
  * call clears the counter and status word on its stream before its kernel.
  * Calls that overlap on the GPU (unordered streams) race on the counter, so
- * order them.  The device status word is not reported by this entry point.
+ * order them.  The device status word (DWTFUSE_EDEVICE when a scene-table
+ * entry failed its device-side check, the scene's outputs then unwritten) is
+ * read by dwtfuse_get_last_device_status(NULL, stream).
  */
 #define DWTFUSE_STATIC_SCRATCH_BYTES 256
 int dwtfuse_fuse_batched_noalloc(const dwtfuse_scene *scenes, int n, int rows_per_item,

@@ -472,8 +472,10 @@ def dwtfuse_qnr(fused: torch.Tensor, ms, pan: torch.Tensor, workspace: torch.Ten
     return q.value, dl.value, ds.value
 
 
-def dwtfuse_get_last_device_status(workspace: torch.Tensor, stream=None) -> int:
-    return int(lib().dwtfuse_get_last_device_status(_dev(workspace, "workspace"), _stream(stream)))
+def dwtfuse_get_last_device_status(workspace: torch.Tensor | None, stream=None) -> int:
+    """Status word of a batched workspace; None: of the last no-alloc batched call."""
+    ws = None if workspace is None else _dev(workspace, "workspace")
+    return int(lib().dwtfuse_get_last_device_status(ws, _stream(stream)))
 
 
 def dwtfuse_set_rows_per_item(rows: int) -> None:

@@ -12,6 +12,9 @@
 
 namespace dwtfuse {
 
+// Defined in fuse_static.cu.
+int noalloc_device_status(cudaStream_t stream);
+
 namespace {
 std::mutex g_mu;
 std::unordered_map<const void *, int> g_occ;
@@ -567,9 +570,9 @@ int dwtfuse_fuse_batched(const dwtfuse_scene *scenes, int n, void *workspace, si
 }
 
 int dwtfuse_get_last_device_status(const void *workspace, void *stream) {
-    if (!workspace) return DWTFUSE_EINVAL;
-    int v = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!workspace) return noalloc_device_status(s);  // the no-alloc call's static array
+    int v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(workspace) + 8, sizeof v,
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -48,6 +48,22 @@ int scratch_address(void **out) {
 }
 
 }  // namespace
+
+// Status word of the last dwtfuse_fuse_batched_noalloc call on the current
+// device, read synchronously on `stream` (a copy from the static array;
+// nothing is allocated).
+int noalloc_device_status(cudaStream_t stream) {
+    void *scratch = nullptr;
+    const int st = scratch_address(&scratch);
+    if (st != DWTFUSE_OK) return st;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, static_cast<const char *>(scratch) + 8, sizeof v, cudaMemcpyDeviceToHost,
+                                    stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return v;
+}
+
 }  // namespace dwtfuse
 
 using namespace dwtfuse;

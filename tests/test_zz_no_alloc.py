@@ -8,7 +8,8 @@ device array instead.  This test calls it through the C ABI twice in a row and
 checks both results against the workspace entry point's on the same scenes:
 the two run the same kernel on the same scene table, so the outputs must be
 equal bit for bit.  The second call must not change how much device memory
-torch's allocator holds or how much the device reports free.
+torch's allocator holds or how much the device reports free, and the status
+word each call leaves in the static array reads back as OK.
 The file is named to be collected last.
 """
 import ctypes
@@ -62,6 +63,8 @@ def test_noalloc_batched_matches_workspace_batched_twice():
         after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
         if call == 1:
             assert after == before, (before, after)
+        # the call's device status word, read from the library's static array
+        assert L.dwtfuse_get_last_device_status(None, stream) == _C.OK
         for sp, a, b in zip(specs, got, ref):
             assert torch.equal(a, b), (call, sp)
 
