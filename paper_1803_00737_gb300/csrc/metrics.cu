@@ -753,10 +753,12 @@ metrics_pan_u8_kernel(const __grid_constant__ MetricArgs a) {
     }
 }
 
-// MS-resolution pass: up to 6 bands, 8-warp CTAs, two per SM (the half of an
-// SM that the fused forward's first finished CTA frees is enough for one, so
-// as a programmatic dependent it starts in that kernel's tail: 16384^2 x 6
-// step 1.687 -> 1.650 ms against 16-warp CTAs).
+// MS-resolution pass: up to 6 bands, 8-warp CTAs, two per SM.  Against
+// 16-warp CTAs, one per SM: faster alone (bench.py --case score_finish,
+// 16384^2 x 6 0.155 -> 0.151 ms, 8192^2 0.076 -> 0.068 ms), and as a
+// programmatic dependent of a primary with two CTAs per SM it can start when
+// either of them has finished (step 1.687 -> 1.650 ms when the fused forward
+// ran 8-warp CTAs; its 16-warp TMEM CTAs free whole SMs only).
 template <int NB, bool GEN>
 struct FastMs {
     static constexpr int K = NB + 1, P = NB * (NB - 1) / 2 + NB;
