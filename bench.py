@@ -790,6 +790,14 @@ def run_case(args) -> None:
         _C.dwtfuse_fuse_and_score(pan, ms, WAVELET, of, ou, ws)
         call = lambda: _C.dwtfuse_score_finish(ms, pan, ou, ws, res)  # noqa: E731
         nbytes = H * W * (B * 0.25 + 1.0)  # MS bands and PAN read once
+    elif args.case == "batched_f32":  # the autograd form's forward: float inputs, one batched launch
+        P = torch.stack([pan.float() for _ in range(args.scenes)])
+        M = torch.stack([ms.float() for _ in range(args.scenes)])
+        of = torch.empty((args.scenes, B, H, W), dtype=torch.float32, device=dev)
+        ws = torch.zeros(_C.dwtfuse_batched_workspace_size(), dtype=torch.uint8, device=dev)
+        scenes = [_C.make_scene(P[i], M[i], WAVELET, of[i], None) for i in range(args.scenes)]
+        call = lambda: _C.dwtfuse_fuse_batched(scenes, ws)  # noqa: E731
+        nbytes = args.scenes * H * W * (4.0 + B * (1.0 + 4.0))
     elif args.case in ("dwt2", "idwt2"):
         Z = torch.empty((H, W), dtype=torch.float32, device=dev)
         _C.dwtfuse_dwt2(pan, WAVELET, Z)
@@ -853,11 +861,12 @@ def main() -> None:
                     help="shrink the batched and autograd workloads (profiling only)")
     ap.add_argument("--side", type=int, default=16384,
                     help="PAN side (default: the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--case", choices=["metrics", "fuse", "fuse_score", "score_finish", "backward", "dwt2", "idwt2",
-                                       "rows"],
+    ap.add_argument("--case", choices=["metrics", "fuse", "fuse_score", "score_finish", "batched_f32", "backward",
+                                       "dwt2", "idwt2", "rows"],
                     help="time one library call alone at --side x --width with --bands (profiling aid)")
     ap.add_argument("--width", type=int, default=0, help="PAN width of a --case run (default: --side)")
     ap.add_argument("--bands", type=int, default=BANDS, help="MS bands of a --case run")
+    ap.add_argument("--scenes", type=int, default=8, help="scenes of a --case batched_f32 run")
     ap.add_argument("--rows", type=int, default=0, help="rows-per-item knob of a --case run (0: default)")
     ap.add_argument("--fwd-chunk", type=int, default=0, help="forward band-chunk knob of a --case run")
     ap.add_argument("--bwd-chunk", type=int, default=0, help="adjoint band-chunk knob of a --case run")
