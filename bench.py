@@ -330,7 +330,10 @@ def measure_e2e(args, pan, ms, out_f, mws, stream, world, dev) -> dict:
             res_h[i].copy_(res_d[i], non_blocking=True)
             downloaded[i].record(s_out)
 
-    warm = max(2, args.warmup)  # pipelined warm-up steps (first touches of the pinned buffers)
+    # Warm-up: pipelined steps (first touches of the pinned buffers), then one
+    # untimed run of Ke steps (the first run over a cold host link measured
+    # about half the rate of the runs after it).
+    warm = max(2, args.warmup) + Ke
     for k in range(warm):
         one(k)
     torch.cuda.synchronize()
