@@ -8,6 +8,8 @@ namespace dwtfuse {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kAltMaxBands = 6;  // widest band chunk of the shifted-row instance
+constexpr int kBatchNarrowBands = 4;     // batched instance for tables of at most 4 bands per entry
+constexpr int kBatchNarrowThreads = 320;  // ... and its CTA size (two per SM)
 
 // Single scene, bands [b0, b0 + NB).  Each warp takes work items
 // warp, warp + total_warps, ... (grid sized to the resident capacity).
@@ -24,7 +26,12 @@ fuse_fwd_kernel(const __grid_constant__ SceneArgs s, int b0, int64_t strips_x, i
 // Batched: every warp pulls the next item index from `queue[0]`; item ranges
 // of the scenes are given by the prefix sums item_start[].  A warp whose
 // scene table entry fails its checks records DWTFUSE_EDEVICE in status[0].
-__global__ void __launch_bounds__(kThreads, 2)
+// MAXB: the most bands of a table entry the instance handles; its registers
+// are those of its widest body, so a table of at most 4 bands per entry runs
+// an instance of 4 with 320-thread CTAs (20 warps per SM at up to 96
+// registers instead of 16 at 128).
+template <int MAXB, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2)
 fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *queue, int *status) {
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)t.item_start[t.n];
@@ -39,7 +46,7 @@ fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *qu
             if ((unsigned long long)t.item_start[mid] <= it) lo = mid; else hi = mid - 1;
         }
         const SceneArgs &s = t.scenes[lo];
-        if (s.bands < 1 || s.bands > kBatchMaxBands) {
+        if (s.bands < 1 || s.bands > MAXB) {
             if (lane == 0) atomicCAS(status, 0, 7);
             continue;
         }
@@ -50,6 +57,7 @@ fuse_batched_kernel(const __grid_constant__ BatchTable t, unsigned long long *qu
         const int nb = s.bands;
 #define DWTFUSE_CASE(NBV)                                                                    \
     case NBV:                                                                                \
+        if constexpr (NBV > MAXB) break;                                                     \
         if constexpr (NBV <= kBatchAltMaxBands) {                                            \
             if (s.alt && !s.a4) {                                                            \
                 if (s.in_f32) {                                                              \
@@ -155,9 +163,14 @@ cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream
 
 cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
                                 int blocks_per_sm, cudaStream_t stream) {
-    void *fn = reinterpret_cast<void *>(&fuse_batched_kernel);
+    int maxb = 0;
+    for (int i = 0; i < t.n; ++i) maxb = t.scenes[i].bands > maxb ? t.scenes[i].bands : maxb;
+    const bool narrow = maxb <= kBatchNarrowBands;
+    const int threads = narrow ? kBatchNarrowThreads : kThreads;
+    void *fn = narrow ? reinterpret_cast<void *>(&fuse_batched_kernel<kBatchNarrowBands, kBatchNarrowThreads>)
+                      : reinterpret_cast<void *>(&fuse_batched_kernel<kBatchMaxBands, kThreads>);
     int occ = 0;
-    cudaError_t e = resident_blocks(fn, kThreads, &occ);
+    cudaError_t e = resident_blocks(fn, threads, &occ);
     if (e != cudaSuccess) return e;
     if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
     int sms = 0;
@@ -166,12 +179,12 @@ cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, 
     e = cudaMemsetAsync(queue, 0, kQueueBytes, stream);
     if (e != cudaSuccess) return e;
     const int64_t total = t.item_start[t.n];
-    const int64_t need = (total + kWarps - 1) / kWarps;
+    const int64_t need = (total + threads / 32 - 1) / (threads / 32);
     const int64_t cap = (int64_t)sms * occ;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
     if (grid == 0) return cudaSuccess;
-    fuse_batched_kernel<<<grid, kThreads, 0, stream>>>(t, queue, status);
-    return cudaGetLastError();
+    void *args[] = {const_cast<BatchTable *>(&t), &queue, &status};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, stream);
 }
 
 }  // namespace dwtfuse
