@@ -31,7 +31,10 @@ ROWS = (8, 16, 24, 32, 48, 64)
 BLOCKS = (0,)  # 0 = as many CTAs per SM as fit
 FWD_CHUNKS = (0, 6, 4)  # 0 = library default (8 bands per launch, 6 on shifted rows)
 BWD_CHUNKS = (0, 4)     # 0 = library default (8)
-CACHE_VERSION = 2
+# Bumped when the kernels behind the knobs change enough that cached choices
+# may no longer be the fastest (3: TMEM scoring kernel, narrow batched
+# instance).
+CACHE_VERSION = 3
 
 _lock = threading.Lock()
 

@@ -50,7 +50,8 @@ def test_cache_round_trip_and_reuse(tmp_path):
 
 
 @pytest.mark.parametrize("content", ["{not json", "[]", '{"version": 1, "entries": {}}',
-                                     '{"version": 2, "entries": {"k": {"rows_per_item": "x"}}}'])
+                                     '{"version": %d, "entries": {"k": {"rows_per_item": "x"}}}'
+                                     % tune.CACHE_VERSION])
 def test_corrupt_cache_is_rebuilt(tmp_path, content):
     path = tmp_path / "t.json"
     path.write_text(content)
