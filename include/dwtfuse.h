@@ -290,12 +290,14 @@ size_t dwtfuse_batched_workspace_size(void);
 
 /*
  * Batched fused forward: up to DWTFUSE_MAX_SCENES scenes of any legal sizes,
- * band counts (<= 8 per scene), wavelets and input types in ONE persistent
- * launch.  Warps pull (scene, tile) work items from a device-side queue whose
- * counter lives in `workspace`; the scene table travels in the kernel's
- * parameter block, so the call is capturable in a CUDA graph (the capture
- * records a memset of the counter and the kernel; the host array `scenes`
- * may be freed after the call).  Results equal dwtfuse_fuse per scene.
+ * band counts (<= 8 per scene), wavelets and input types in one persistent
+ * launch (two when the table mixes entries of at most 4 bands with wider
+ * ones: each set runs the kernel instance sized for it).  Warps pull (scene,
+ * tile) work items from a device-side queue whose counter lives in
+ * `workspace`; the scene table travels in the kernel's parameter block, so the
+ * call is capturable in a CUDA graph (the capture records memsets of the
+ * counter and the kernels; the host array `scenes` may be freed after the
+ * call).  Results equal dwtfuse_fuse per scene.
  *   rows_per_item  MS rows per work item (0 = library default)
  *   blocks_per_sm  resident CTAs per SM for the persistent grid (0 = max)
  */

@@ -161,8 +161,14 @@ cudaError_t launch_fuse(const SceneArgs &s, int R, int blocks_per_sm, cudaStream
     return cudaSuccess;
 }
 
-cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
-                                int blocks_per_sm, cudaStream_t stream) {
+namespace {
+
+// One launch over table t: the narrow instance when every entry has at most
+// kBatchNarrowBands bands.  clear: bytes of the queue word(s) to zero first
+// (the queue counter and status word, or only the counter so that a status an
+// earlier launch of the same call recorded survives).
+cudaError_t launch_table(const BatchTable &t, unsigned long long *queue, int *status, int blocks_per_sm,
+                         size_t clear, cudaStream_t stream) {
     int maxb = 0;
     for (int i = 0; i < t.n; ++i) maxb = t.scenes[i].bands > maxb ? t.scenes[i].bands : maxb;
     const bool narrow = maxb <= kBatchNarrowBands;
@@ -176,7 +182,7 @@ cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, 
     int sms = 0;
     e = sm_count(&sms);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(queue, 0, kQueueBytes, stream);
+    e = cudaMemsetAsync(queue, 0, clear, stream);
     if (e != cudaSuccess) return e;
     const int64_t total = t.item_start[t.n];
     const int64_t need = (total + threads / 32 - 1) / (threads / 32);
@@ -185,6 +191,38 @@ cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, 
     if (grid == 0) return cudaSuccess;
     void *args[] = {const_cast<BatchTable *>(&t), &queue, &status};
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, stream);
+}
+
+// The entries of t with (narrow) or without at most kBatchNarrowBands bands.
+void split_table(const BatchTable &t, bool narrow, BatchTable *o) {
+    o->n = 0;
+    o->R = t.R;
+    o->item_start[0] = 0;
+    for (int i = 0; i < t.n; ++i) {
+        if ((t.scenes[i].bands <= kBatchNarrowBands) != narrow) continue;
+        o->scenes[o->n] = t.scenes[i];
+        o->strips_x[o->n] = t.strips_x[i];
+        o->item_start[o->n + 1] = o->item_start[o->n] + (t.item_start[i + 1] - t.item_start[i]);
+        ++o->n;
+    }
+}
+
+}  // namespace
+
+// A table mixing entries of at most kBatchNarrowBands bands with wider ones
+// runs as two launches: the narrow entries on the narrow instance, the rest on
+// the 8-band one.
+cudaError_t launch_fuse_batched(const BatchTable &t, unsigned long long *queue, int *status,
+                                int blocks_per_sm, cudaStream_t stream) {
+    int nn = 0;
+    for (int i = 0; i < t.n; ++i) nn += t.scenes[i].bands <= kBatchNarrowBands;
+    if (nn == 0 || nn == t.n) return launch_table(t, queue, status, blocks_per_sm, kQueueBytes, stream);
+    static thread_local BatchTable part;
+    split_table(t, false, &part);
+    cudaError_t e = launch_table(part, queue, status, blocks_per_sm, kQueueBytes, stream);
+    if (e != cudaSuccess) return e;
+    split_table(t, true, &part);
+    return launch_table(part, queue, status, blocks_per_sm, sizeof(unsigned long long), stream);
 }
 
 }  // namespace dwtfuse
