@@ -220,3 +220,27 @@ def test_benchmark_step_full_size(ws):
     ref = np.array([O.ergas(f, list(m)), q, dl, ds])
     assert abs(r[0] - ref[0]) <= 1e-12 * ref[0], (r, ref)
     assert np.abs(r[1:] - ref[1:]).max() <= 2e-6, (r, ref)
+
+
+@pytest.mark.parametrize("B", [2, 6, 8])
+def test_two_streams_at_once(ws, B):
+    """Two scoring calls on two streams at the same time give the results of
+    the calls one after the other.  Each CTA of the scoring kernel allocates
+    tensor memory (TMEM) and takes more than half of an SM's registers, so
+    CTAs of the two launches never share an SM."""
+    pan, ms = scene(512, 1024, B, seed=40 + B)
+    ws2 = torch.empty_like(ws)
+    f1, u1, r1 = fused_path(pan, ms, O.D4, ws)
+    Bn, (H, W) = ms.shape[0], pan.shape
+    outs = [(torch.empty((Bn, H, W), device=DEV), torch.empty((Bn, H, W), dtype=torch.uint8, device=DEV),
+             torch.full((4,), float("nan"), dtype=torch.float64, device=DEV)) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    for k in range(3):
+        for (of, ou, res), st, w in zip(outs, streams, (ws, ws2)):
+            with torch.cuda.stream(st):
+                _C.dwtfuse_fuse_metrics(pan, ms, O.D4, of, ou, w, res, stream=st)
+    torch.cuda.synchronize()
+    for of, ou, res in outs:
+        assert torch.equal(of, f1) and torch.equal(ou, u1)
+        assert np.array_equal(res.cpu().numpy(), r1)
