@@ -87,3 +87,17 @@ def test_dram_traffic_record_matches_the_kernel_sources():
     t = bench.KNOWN_TRAFFIC[bench.kernel_hash()]
     alg = bench.fwd_bytes_per_launch()
     assert 0.95 * alg <= t <= 1.05 * alg  # DRAM bytes per launch near the algorithmic bytes
+
+
+def test_every_case_choice_has_a_branch():
+    """Each --case name bench.py accepts is handled by run_case (the backward
+    case is its final else branch)."""
+    import inspect
+    import re
+    choices = re.search(r'"--case", choices=\[([^\]]*)\]', inspect.getsource(bench.main), re.S).group(1)
+    names = re.findall(r'"(\w+)"', choices)
+    assert "batched_f32" in names and "score_finish" in names
+    src = inspect.getsource(bench.run_case)
+    for n in names:
+        if n != "backward":
+            assert f'"{n}"' in src, n
