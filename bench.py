@@ -85,6 +85,9 @@ KNOWN_TRAFFIC: dict[str, float] = {
     # the same 6-band body after 8 bands joined the TMEM kernel (12-warp CTAs):
     # read 689,428,992 + write 7,989,767,594 (mean of 3 launches)
     "117fcefd467f": 8679196586.0,
+    # the same kernel waiting for its TMEM stores before every scoring:
+    # read 689,644,885 + write 7,989,676,288 (mean of 3 launches)
+    "22e4d6d25dce": 8679321173.0,
 }
 KERNEL_SOURCES = ("fuse_tile.cuh", "fuse_metrics.cu", "metric_q.cuh", "tmem.cuh")
 

@@ -114,7 +114,6 @@ __device__ __forceinline__ void metric_pan(uint32_t *tile, int lane, int r, cons
     tile[(NB * 2 * SR + 2 * r + 1) * 32 + lane] = pack4(f2u8(pan1[0]), f2u8(pan1[1]), f2u8(pan1[2]), f2u8(pan1[3]));
 }
 
-
 template <int NB>
 struct FmLayout {
     static constexpr int K = NB + 1;                  // images: NB bands, then PAN
@@ -122,8 +121,10 @@ struct FmLayout {
     static constexpr int NS = 2 * K + P;              // window sums per lane: S1[K], S2[K], Sxy[P]
     static constexpr int NT = NS + NB;                // TMEM cells per lane: window sums, squared errors
     // MS rows parked before they are scored (divides 16): 4 rows of 6 bands
-    // take 12.4 KB of shared memory per warp, 7 bands park 2.
+    // take 12.4 KB of shared memory per warp; 7-8 bands park 2.
     static constexpr int SR = NB <= 6 ? 4 : 2;
+    // One CTA per SM (it holds TMEM): 16 warps at up to 128 registers, 8
+    // bands 12 warps at up to 168 (the 8-band walker spills at 128).
     static constexpr int kThreads = NB <= 7 ? 512 : 384;
     static constexpr int kWarps = kThreads / 32;
     // Per-warp shared memory (32-bit words, lane-minor so that lane accesses are conflict-free).
@@ -134,7 +135,7 @@ struct FmLayout {
     static constexpr int kWords = (kTile + kRep + kGsum + kQ + 1) & ~1;
     static constexpr int kWarpBytes = kWords * 4 + NB * 32 * 8;  // + int64 squared errors per lane
     static constexpr int kSmem = kWarps * kWarpBytes + 16;     // + the TMEM base address
-    // TMEM: warps w, w + 4, w + 8, w + 12 share a quarter of the lanes, side by side.
+    // TMEM: warps w, w + 4, w + 8, ... share a quarter of the lanes, side by side.
     static constexpr int kWarpTmem = fm_pow2_at_least(NT, 16);
     static constexpr int kTmemCols = fm_pow2_at_least((kWarps + 3) / 4 * kWarpTmem, 32);
     static_assert(NT <= 64 && kTmemCols <= 512, "TMEM columns of an SM");
@@ -211,11 +212,11 @@ struct MetricEmit {
     __device__ __forceinline__ void score_cells(int nr, bool fl, bool win_in) const {
         constexpr int N = HI - LO, NE = SE ? NB : 0;
         uint32_t a[N + NE];
+        tm_wait_st();  // this lane's earlier stores to these cells are done (read or overwritten next)
         if (fresh) {
 #pragma unroll
             for (int k = 0; k < N + NE; ++k) a[k] = 0;
         } else {
-            tm_wait_st();
             tm_issue<N>(taddr + LO, a);
             if constexpr (SE) tm_issue<NB>(taddr + NS, a + N);
             tm_wait_ld<N + NE>(a);
